@@ -1,0 +1,403 @@
+"""Benchmark of the CHYM GB300 simulator on the N=100 workload.
+
+Workload (one bench step): the Moebius ladder N=100 (ring bonds -1 plus
+antipodal rungs -1) and an SK +-1 N=100 instance, each at hyperspin dimension
+D in {2 (XY machine, no annealing), 3, 4} with 4096 runs = 32 pump values x
+128 replicas, 20000 Euler-Maruyama steps (dt = 0.01; D >= 3 anneal linearly
+over the second half), then Ising readout, energies and ground-state hit
+statistics.  Metric: hyperspin-steps/s (N * D * runs * steps per second) and
+ground-state hits per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x2|fp32]
+  python bench.py --impl reference ...   # the FP64 CPU checker on host cores
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload with its
+own seeds (runs are independent); value = all ranks' work / max rank time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GS hits/s and hyperspin-steps/s (N·D·runs·steps), mixed+learned vs plain FP32"
+UNIT = "hyperspin-steps/s"
+N_SPINS = 100
+D_LIST = (2, 3, 4)
+N_H = 32
+REPS = 128
+STEPS = 20000
+EPS_HAT = 0.5
+INSTANCE_SEED = 0xC0FFEE
+
+
+def workload_config(prec_name):
+    return {"workload": "moebius N=100 + SK+-1 N=100, D in {2,3,4}, 4096 runs/graph "
+                        "(32 h x 128 replicas), 20000 steps dt=0.01",
+            "graphs": ["moebius_ladder_100", "sk_pm1_100"], "D": list(D_LIST),
+            "runs_per_graph": N_H * REPS, "n_h": N_H, "replicas": REPS, "steps": STEPS,
+            "precision": prec_name, "l2": "flushed between steps (256 MiB write)"}
+
+
+def make_instances(rank):
+    from paper_2308_02329_gb300 import inputs
+    return [("moebius", inputs.mobius_ladder(N_SPINS)),
+            ("sk", inputs.sk_pm1(N_SPINS, INSTANCE_SEED + 1 + 1000 * rank))]
+
+
+def mode_for(D):
+    """D = 2: XY machine without annealing (kappa L = 1e-3); D >= 3: annealing mode
+    (kappa L = 0.1); beta b^2 = 25 in both."""
+    if D == 2:
+        return 1e-3, 0
+    return 0.1, 1
+
+
+def alu_ops_per_element(D, nnz_row, coupling_on_alu):
+    """Algorithmic ALU lane-operations per element-step (one x_{p,mu} advanced once).
+
+    Noise: one Philox4x32-10 block (10 rounds x [2 wide multiplies + 2 three-input
+    xors + 2 key adds] = 60 ops) per spin per 4 components, Box-Muller 12 ops per pair
+    (2 int->float, 2 scalings, log, radius scaling, sqrt, angle, sin, cos, 2 products).
+    Drift + Euler-Maruyama update: 6.5 ops (norm share, x^2, cubic/loss FMA, product,
+    coupling FMA, noise add).  Coupling on the ALU adds nnz_row FMAs (dense J: N)."""
+    blocks = -(-D // 4)
+    pairs = -(-D // 2)
+    ops = 60.0 * blocks / D + 12.0 * pairs / D + 6.5
+    if coupling_on_alu:
+        ops += nnz_row
+    return ops
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline_sample(target_s=10.0, threads=None):
+    """Time the FP64 CPU checker on a bounded sample of the same workload (all host cores)."""
+    import oracle.oracle as O
+    from paper_2308_02329_gb300 import inputs
+    threads = threads or os.cpu_count()
+    J = inputs.sk_pm1(N_SPINS, INSTANCE_SEED + 1)
+    lam = float(np.linalg.eigvalsh(J)[-1])
+    D = 4
+    prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=0.1, eps=EPS_HAT / lam)
+    sched = O.Schedule(1, STEPS // 2, STEPS)
+    h = inputs.pump_grid(1.0 - EPS_HAT, N_H)
+
+    def timed(runs, steps):
+        seeds = inputs.run_seeds(INSTANCE_SEED, runs)
+        hr = np.resize(np.repeat(h, max(1, runs // N_H)), runs)
+        X = O.init_state(N_SPINS, D, seeds, prm.init_std)
+        t0 = time.perf_counter()
+        O.integrate(J, X, hr, seeds, prm, sched, 0, steps, threads=threads)
+        return time.perf_counter() - t0
+
+    runs = max(threads * 2, 16)
+    probe_steps = 20
+    dt_probe = timed(runs, probe_steps)
+    steps = int(max(probe_steps, min(STEPS, probe_steps * target_s / max(dt_probe, 1e-6))))
+    el = timed(runs, steps)
+    value = N_SPINS * D * runs * steps / el
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"SK+-1 N=100 D=4, {runs} runs x {steps} steps (annealed from step "
+                      f"{STEPS // 2}), FP64, OpenMP over runs; {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU checker as it stands, timed on the host cores on this workload."""
+    if rank != 0:
+        return 0
+    import oracle.oracle as O
+    from paper_2308_02329_gb300 import inputs
+    threads = os.cpu_count()
+    insts = make_instances(0)
+    prepared = []
+    for name, J in insts:
+        lam = float(np.linalg.eigvalsh(J)[-1])
+        for D in D_LIST:
+            kappa, kind = mode_for(D)
+            prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
+                           eps=EPS_HAT / lam)
+            prepared.append((J, D, prm, O.Schedule(kind, STEPS // 2, STEPS)))
+    h = inputs.pump_grid(1.0 - EPS_HAT, N_H)
+    runs = max(threads, 16)
+    seeds = inputs.run_seeds(INSTANCE_SEED, runs)
+    hr = np.resize(np.repeat(h, max(1, runs // N_H)), runs)
+    # size each step to about 6 s of wall time
+    t0 = time.perf_counter()
+    for J, D, prm, sch in prepared:
+        X = O.init_state(N_SPINS, D, seeds, prm.init_std)
+        O.integrate(J, X, hr, seeds, prm, sch, 0, 50, threads=threads)
+    per_50 = time.perf_counter() - t0
+    steps = int(max(50, min(STEPS, 50 * 6.0 / max(per_50, 1e-6))))
+    work = sum(N_SPINS * D * runs * steps for _, D, _, _ in prepared)
+
+    def one():
+        for J, D, prm, sch in prepared:
+            X = O.init_state(N_SPINS, D, seeds, prm.init_std)
+            O.integrate(J, X, hr, seeds, prm, sch, 0, steps, threads=threads)
+            O.ising_energies(J, O.readout(X))
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    value = work * args.steps / el
+    sample = (f"per step: 2 graphs x D in {{2,3,4}}, {runs} runs x {steps} steps each "
+              f"(of 4096 x 20000), FP64, OpenMP over runs")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config("fp64 (CPU checker)"),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="chym", choices=["chym", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["bf16x2", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sim-steps", type=int, default=STEPS, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2308_02329_gb300 import chym, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    prec = chym.PREC_BF16X2 if args.prec == "bf16x2" else chym.PREC_FP32
+    sim_steps = args.sim_steps
+
+    # ---------------- setup (untimed): instances, references, device inputs -------------
+    jobs = []
+    for gi, (name, J) in enumerate(make_instances(rank)):
+        for D in D_LIST:
+            ctx = chym.Context(J, D, chym.J_PM1)
+            lam = ctx.lambda_max()
+            kappa, kind = mode_for(D)
+            prm = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
+                              eps=EPS_HAT / lam, prec=prec)
+            sched = chym.Schedule(kind, sim_steps // 2 if kind else 0, sim_steps)
+            h = inputs.pump_grid(1.0 - EPS_HAT, N_H)
+            seeds = inputs.run_seeds(INSTANCE_SEED + 7919 * rank + 97 * gi + D, N_H * REPS)
+            d_h = torch.from_numpy(h).to(dev)
+            d_seeds = torch.from_numpy(seeds.view(np.int64)).to(dev)
+            d_E = torch.empty(N_H * REPS, dtype=torch.float64, device=dev)
+            jobs.append(dict(name=name, J=J, D=D, ctx=ctx, prm=prm, sched=sched, h=h, seeds=seeds,
+                             d_h=d_h, d_seeds=d_seeds, d_E=d_E, nnz=int((J != 0).sum(1).mean())))
+    gs = {}
+    for name, J in make_instances(rank):
+        if name == "moebius":
+            gs[name] = chym.ground_state_mobius(N_SPINS)
+        else:
+            c1 = chym.Context(J, 1)
+            gs[name] = c1.ground_state_search(restarts=64, sweeps=2000, seed=11)[0]
+            c1.close()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    ev = []
+
+    def one_step(record=False):
+        """init + sim_steps steps + energy + stats for every (graph, D); device inputs.
+        Returns the ground-state hits of this step."""
+        flush.fill_(1.0)
+        hits = 0
+        for j in jobs:
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), N_H, j["d_seeds"].data_ptr(),
+                                N_H * REPS, sim_steps, j["sched"], sp)
+            if record:
+                e1.record(stream)
+                ev.append((j, e0, e1))
+            j["ctx"].energy_device(j["d_E"].data_ptr(), 0, sp)
+            if record:
+                hits += int(j["ctx"].stats(gs[j["name"]], 0, sp)["n_hits"])
+        return hits
+
+    # warm-up; the SK reference also takes the best energy the runs found (best known)
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    for j in jobs:
+        if j["name"] == "sk":
+            gs["sk"] = min(gs["sk"], float(j["d_E"].min().item()))
+
+    # ---------------- timed region: device-resident inputs ----------------
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    hits_total = 0
+    for _ in range(args.steps):
+        hits_total += one_step(record=True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        ht = torch.tensor([hits_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(ht)
+        hits_total = int(ht.item())
+
+    work_step = sum(N_SPINS * j["D"] * N_H * REPS * sim_steps for j in jobs)
+    value = work_step * args.steps * world / elapsed
+    # roofline of the dominant kernel (the step kernel), from its launches' events
+    dur = sum(e0.elapsed_time(e1) / 1e3 for _, e0, e1 in ev)
+    on_alu = prec == chym.PREC_FP32
+    alg = sum(alu_ops_per_element(j["D"], N_SPINS if j["name"] == "sk" else j["nnz"], on_alu) *
+              N_SPINS * j["D"] * N_H * REPS * sim_steps for j, _, _ in ev)
+    achieved = alg / dur
+    sm_mhz = clock_info.get("sm_mhz") or 1440.0
+    peak = 152 * 128 * sm_mhz * 1e6
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "Tlane-op/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "chym step kernel (" + args.prec + ")",
+                "peak_note": "152 SMs x 128 FP32 lanes x median SM clock during the region"}
+
+    # ---------------- e2e: host inputs through the public API ----------------
+    e2e = None
+    if not args.no_e2e:
+        pin_h = [torch.from_numpy(j["h"]).pin_memory() for j in jobs]
+        pin_s = [torch.from_numpy(j["seeds"].view(np.int64)).pin_memory() for j in jobs]
+        E_host = [torch.empty(N_H * REPS, dtype=torch.float64).pin_memory() for _ in jobs]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            for j, ph, ps, eh in zip(jobs, pin_h, pin_s, E_host):
+                j["ctx"].run(j["prm"], ph.numpy(), ps.numpy().view(np.uint64), sim_steps,
+                             j["sched"], sp)
+                Eh = j["ctx"].energy(stream=sp)
+                eh.copy_(torch.from_numpy(Eh))
+                j["ctx"].stats(gs[j["name"]], 0, sp)
+        torch.cuda.synchronize()
+        el2 = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el2], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el2 = float(t.item())
+        h2d = sum(N_H * 8 + N_H * REPS * 8 for _ in jobs)
+        d2h = sum(N_H * REPS * 8 + 64 + N_H * 8 for _ in jobs)
+        e2e = {"value": work_step * args.steps * world / el2, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline_sample()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16x2+f32" if prec == chym.PREC_BF16X2 else "f32",
+                "data": "synthetic", "config": workload_config(args.prec),
+                "gs_hits_per_s": hits_total / elapsed,
+                "e_gs": {k: float(v) for k, v in gs.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+                "gpu_launches": 4 * len(jobs) * args.steps}
+        print(json.dumps(line), flush=True)
+    for j in jobs:
+        j["ctx"].close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

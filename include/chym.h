@@ -1,0 +1,197 @@
+/*
+ * chym.h -- C ABI of the GB300 simulator of the coherent hyperspin machine
+ * (CHYM) of "Hyperscaling in the coherent hyperspin machine" (Calvanese
+ * Strinati & Conti, arXiv 2308.02329).
+ *
+ * The library integrates many independent runs (replicas x pump values h) of
+ * the CHYM equations for one coupling matrix J_N and one hyperspin dimension
+ * D, then reads out the Ising spins, their Ising energy and the ground-state
+ * hit statistics.  Plain C types only: pointers are host pointers unless the
+ * name of the entry point ends in _device, sizes are element counts.
+ *
+ * Model (one run, hyperspin p = 0..N-1, component mu = 0..D-1, step k):
+ *   y_{p,mu} = sum_q J_pq x_{q,mu}                      coupling C = J_N (x) 1_D (Eq. 1)
+ *   n_p      = sum_nu x_{p,nu}^2                        non-local loss W = beta 1_N (x) I_D (Eq. 1)
+ *   x_{p,mu} <- x_{p,mu} + dt [ (h-1) x_{p,mu} - kappa x_{p,mu}^3 - gamma x_{p,mu} n_p
+ *                              + eps alpha_mu(k) y_{p,mu} ] + sigma sqrt(dt) xi
+ * i.e. the round-trip map of Eq. 2 read as the Euler-Maruyama step of its
+ * continuous-time limit (gamma stands for beta b^2, kappa for the local
+ * kappa L), with dimensional annealing C -> alpha_mu C (text after Fig. 2)
+ * and additive Gaussian noise xi drawn from Philox4x32-10 (key = run seed,
+ * counter = (p, tag << 8 | mu / 4, k lo, k hi), Box-Muller on the four words).
+ * The Ising readout is s_p = sign(x_{p,0}) (ties to +1) and the energy is
+ * E = -sum_{p,q} J_pq s_p s_q (Eq. 3 with Ising spins).
+ *
+ * Runs are h-major: run = ih * replicas + rep, replicas = n_runs / n_h.
+ *
+ * Errors: every entry point returns a chym_status and never aborts or throws;
+ * on failure chym_last_error() returns a message (thread-local, valid until
+ * the next call on the same thread).  Calls on one context are not
+ * thread-safe; different contexts are independent.
+ */
+#ifndef CHYM_H
+#define CHYM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CHYM_API __attribute__((visibility("default")))
+#else
+#define CHYM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chym_ctx chym_ctx; /* opaque; owns the device copies of J and the run state */
+
+typedef enum {
+  CHYM_OK = 0,
+  CHYM_EINVAL = 1,   /* invalid argument; nothing was launched */
+  CHYM_ENOMEM = 2,   /* host or device allocation failed */
+  CHYM_ECUDA = 3,    /* a CUDA call failed; chym_last_error() has the CUDA message */
+  CHYM_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  CHYM_ENOTSUP = 5,  /* valid request that this build does not implement */
+  CHYM_ESTATE = 6    /* call out of order (e.g. energy before any run) */
+} chym_status;
+
+typedef enum {
+  CHYM_J_PM1 = 0, /* entries in {-1, 0, +1}: energies are exact integers */
+  CHYM_J_REAL = 1 /* arbitrary real couplings: energies accumulate in FP64 */
+} chym_jkind;
+
+typedef enum {
+  CHYM_PREC_FP64 = 0,   /* FP64 state and arithmetic (checker-comparison mode) */
+  CHYM_PREC_FP32 = 1,   /* FP32 state, FP32 SIMT coupling product (plain form) */
+  CHYM_PREC_BF16X2 = 2  /* FP32 state; J x on tcgen05 tensor cores with J in BF16 and
+                           x split into BF16 hi + lo, FP32 accumulation */
+} chym_prec;
+
+typedef struct {
+  double dt;       /* Euler-Maruyama time step */
+  double sigma;    /* diffusion coefficient; the per-step noise std is sigma*sqrt(dt) */
+  double init_std; /* std of the initial amplitudes x(0) */
+  double gamma;    /* non-local saturation (beta b^2) */
+  double kappa;    /* local saturation (kappa L) */
+  double eps;      /* feedback coupling strength */
+  int32_t prec;    /* chym_prec */
+  int32_t flags;   /* reserved, must be 0 */
+} chym_params;
+
+typedef struct {
+  int32_t kind;     /* 0: no annealing (alpha = 1); 1: linear */
+  int32_t reserved; /* must be 0 */
+  int64_t k_anneal; /* linear: alpha_mu = 1 for k < k_anneal (mu >= 1) ... */
+  int64_t k_total;  /* ... then 1 - (k - k_anneal)/(k_total - k_anneal), 0 from k_total on */
+} chym_schedule;
+
+typedef struct {
+  double P_max;     /* max over h of P_Ising(h) (figure of merit (i)) */
+  double W_range;   /* figure of merit (ii) normalised by the number of h with P > 0 */
+  double W_scan;    /* figure of merit (ii) normalised by the number of scanned h */
+  double dE_mean;   /* figure of merit (iii): mean E - E_GS over finite runs */
+  double best_E;    /* lowest final Ising energy over all runs */
+  int64_t best_run; /* lowest run index reaching best_E */
+  int64_t n_finite; /* runs whose state stayed finite */
+  int64_t n_hits;   /* runs with E == E_GS */
+} chym_stats_t;
+
+/* Thread-local message describing the last failure on this thread. */
+CHYM_API const char* chym_last_error(void);
+
+/* Create a context for the N x N coupling matrix J (row-major FP64, copied)
+ * and hyperspin dimension D.  J must be symmetric with a zero diagonal
+ * (J_N is the symmetric adjacency matrix of the graph, text after Eq. 1);
+ * kind CHYM_J_PM1 additionally requires entries in {-1,0,1}.
+ * Limits: 1 <= N <= 4096, 1 <= D <= 8.  EINVAL otherwise; ECUDA/ENOMEM on
+ * device failures.  *out is set only on success. */
+CHYM_API chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx** out);
+
+/* Release every device and host resource of ctx (NULL is accepted). */
+CHYM_API chym_status chym_destroy(chym_ctx* ctx);
+
+/* Largest eigenvalue of J (FP64 Lanczos on the host), used for the pump
+ * threshold h_th = 1 - eps * lambda_max of the linearised equations. */
+CHYM_API chym_status chym_lambda_max(chym_ctx* ctx, double* lambda_out);
+
+/* Integrate n_runs runs for `steps` Euler-Maruyama steps on `cuda_stream`
+ * (a cudaStream_t; NULL = default stream).  h: n_h pump values (host);
+ * seeds: n_runs 64-bit noise keys (host).  With seeds != NULL every run is
+ * (re)initialised from its seed at step 0 (x(0) = init_std * N(0,1), tag 1);
+ * with seeds == NULL the existing runs continue from the context's current
+ * step (checkpoint/resume: the noise is counter based, so two calls of K/2
+ * steps equal one call of K) and n_runs must match.  The schedule refers to
+ * absolute steps.  The call is asynchronous with respect to the host except
+ * for the upload of h and seeds.
+ * EINVAL: steps < 0, n_h < 1, n_runs not a multiple of n_h, bad params. */
+CHYM_API chym_status chym_run(chym_ctx* ctx, const chym_params* params, const double* h, int n_h,
+                     const uint64_t* seeds, int n_runs, int64_t steps,
+                     const chym_schedule* schedule, void* cuda_stream);
+
+/* Same as chym_run with h (n_h doubles) and seeds (n_runs uint64) already in
+ * device memory; nothing is copied between host and device. */
+CHYM_API chym_status chym_run_device(chym_ctx* ctx, const chym_params* params, const double* d_h,
+                            int n_h, const uint64_t* d_seeds, int n_runs, int64_t steps,
+                            const chym_schedule* schedule, void* cuda_stream);
+
+/* Ising readout and energy of every run (Eq. 3 with s_p = sign x_{p,0}).
+ * E_out: n_runs doubles (host), exact integers for CHYM_J_PM1, NaN for a run
+ * whose state is not finite.  spins_out: nullable, n_runs * ceil(N/64) words,
+ * bit p of word p/64 set when s_p = +1.  Synchronises the stream. */
+CHYM_API chym_status chym_energy(chym_ctx* ctx, double* E_out, uint64_t* spins_out, void* cuda_stream);
+
+/* Device-memory variant of chym_energy: d_E (n_runs doubles) and nullable
+ * d_spins are device pointers; asynchronous. */
+CHYM_API chym_status chym_energy_device(chym_ctx* ctx, double* d_E, uint64_t* d_spins, void* cuda_stream);
+
+/* Ground-state statistics of the last energies (figures of merit (i)-(iii)
+ * after Fig. 3): hits_per_h (nullable, n_h int64) counts replicas with
+ * E == E_gs (|E - E_gs| <= 1e-9 |E_gs| for real J); hist (nullable, n_bins
+ * int64) is H_E binned by (E - E_gs) / bin_width (4 for +-1 couplings, whose
+ * energies move in steps of 4; 1e-3 |E_gs| otherwise), energies past the last
+ * bin counted in it.  Requires chym_energy or chym_energy_device first.
+ * Synchronises the stream. */
+CHYM_API chym_status chym_stats(chym_ctx* ctx, double E_gs, chym_stats_t* out, int64_t* hits_per_h,
+                       int64_t* hist, int n_bins, void* cuda_stream);
+
+/* Copy the run state to the host as FP64, layout X[run][p][mu] (n_runs*N*D
+ * doubles), and the current step.  Synchronises the stream. */
+CHYM_API chym_status chym_get_state(chym_ctx* ctx, double* X_out, int64_t* k_out, void* cuda_stream);
+
+/* Replace the run state (X[run][p][mu], FP64 host) and the step counter,
+ * e.g. to resume from a checkpoint; the precision of the following chym_run
+ * decides how it is stored.  seeds: n_runs noise keys; h: n_h pumps. */
+CHYM_API chym_status chym_set_state(chym_ctx* ctx, const double* X, int n_runs, const double* h,
+                           int n_h, const uint64_t* seeds, int64_t k, int32_t prec,
+                           void* cuda_stream);
+
+/* Shape of the current batch: n_runs, n_h and the current step (any may be NULL). */
+CHYM_API chym_status chym_info(chym_ctx* ctx, int* n_runs, int* n_h, int64_t* k);
+
+/* ---- Ground-state references (host; E_GS of the success probability
+ * P_Ising, which counts the runs that end at the Ising ground-state energy,
+ * text before Fig. 4).  Energies use E = -sum_{p,q} J_pq s_p s_q. ---- */
+
+/* Exact E_GS of ctx's J by exhaustive Gray-code enumeration of the 2^{N-1}
+ * states (spin N-1 fixed by the global flip symmetry).  N <= 34, EINVAL
+ * otherwise.  spins_out: nullable, ceil(N/64) words, bit p set for s_p = +1. */
+CHYM_API chym_status chym_ground_state_exact(chym_ctx* ctx, double* E_out, uint64_t* spins_out);
+
+/* Exact E_GS of the Moebius ladder (ring bonds j_ring between i and i+1 mod N,
+ * rungs j_rung between i and i+N/2) by a minimisation over rung states along
+ * the ladder.  N even, >= 6. */
+CHYM_API chym_status chym_ground_state_mobius(int N, double j_ring, double j_rung, double* E_out);
+
+/* Best-known E_GS of ctx's J by simulated annealing (restarts x sweeps
+ * single-spin Metropolis sweeps, geometric inverse-temperature ramp, then
+ * greedy descent), deterministic for a given seed.  An upper bound on E_GS. */
+CHYM_API chym_status chym_ground_state_search(chym_ctx* ctx, int restarts, int sweeps, uint64_t seed,
+                                              double* E_out, uint64_t* spins_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHYM_H */

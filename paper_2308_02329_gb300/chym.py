@@ -1,0 +1,245 @@
+"""Thin ctypes binding of the C ABI in ``include/chym.h``.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2308_02329_gb300.build``); a missing library raises, there is
+no fallback.  Device pointers and CUDA streams may come from torch
+(``tensor.data_ptr()``, ``torch.cuda.current_stream().cuda_stream``) or any
+other CUDA runtime user.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libchym.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ESTATE = range(7)
+J_PM1, J_REAL = 0, 1
+PREC_FP64, PREC_FP32, PREC_BF16X2 = 0, 1, 2
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP", 6: "ESTATE"}
+
+EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", "chym_run",
+           "chym_run_device", "chym_energy", "chym_energy_device", "chym_stats",
+           "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
+           "chym_ground_state_mobius", "chym_ground_state_search"]
+
+
+class ChymError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("init_std", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("eps", ctypes.c_double),
+                ("prec", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class CSchedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("k_anneal", ctypes.c_int64), ("k_total", ctypes.c_int64)]
+
+
+class CStats(ctypes.Structure):
+    _fields_ = [("P_max", ctypes.c_double), ("W_range", ctypes.c_double),
+                ("W_scan", ctypes.c_double), ("dE_mean", ctypes.c_double),
+                ("best_E", ctypes.c_double), ("best_run", ctypes.c_int64),
+                ("n_finite", ctypes.c_int64), ("n_hits", ctypes.c_int64)]
+
+
+@dataclass
+class Params:
+    """Model constants (see include/chym.h): gamma = beta b^2, kappa = kappa L."""
+    dt: float = 0.01
+    sigma: float = 1e-3
+    init_std: float = 0.1
+    gamma: float = 25.0
+    kappa: float = 0.1
+    eps: float = 0.05
+    prec: int = PREC_FP32
+
+    def c(self):
+        return CParams(self.dt, self.sigma, self.init_std, self.gamma, self.kappa, self.eps,
+                       int(self.prec), 0)
+
+
+@dataclass
+class Schedule:
+    kind: int = 1
+    k_anneal: int = 0
+    k_total: int = 1
+
+    def c(self):
+        return CSchedule(int(self.kind), 0, int(self.k_anneal), int(self.k_total))
+
+
+_lib = None
+
+
+def lib():
+    """Load libchym.so once; raise if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CHYM CUDA library not built: {LIB_PATH} is missing "
+                              "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.chym_last_error.restype = ctypes.c_char_p
+        L.chym_last_error.argtypes = []
+        L.chym_create.argtypes = [vp, i32, i32, i32, ctypes.POINTER(vp)]
+        L.chym_destroy.argtypes = [vp]
+        L.chym_lambda_max.argtypes = [vp, ctypes.POINTER(dbl)]
+        L.chym_run.argtypes = [vp, ctypes.POINTER(CParams), vp, i32, vp, i32, i64,
+                               ctypes.POINTER(CSchedule), vp]
+        L.chym_run_device.argtypes = L.chym_run.argtypes
+        L.chym_energy.argtypes = [vp, vp, vp, vp]
+        L.chym_energy_device.argtypes = [vp, vp, vp, vp]
+        L.chym_stats.argtypes = [vp, dbl, ctypes.POINTER(CStats), vp, vp, i32, vp]
+        L.chym_get_state.argtypes = [vp, vp, ctypes.POINTER(i64), vp]
+        L.chym_set_state.argtypes = [vp, vp, i32, vp, i32, vp, i64, ctypes.c_int32, vp]
+        L.chym_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        L.chym_ground_state_exact.argtypes = [vp, ctypes.POINTER(dbl), vp]
+        L.chym_ground_state_mobius.argtypes = [i32, dbl, dbl, ctypes.POINTER(dbl)]
+        L.chym_ground_state_search.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp]
+        for name in EXPORTS:
+            if name != "chym_last_error":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise ChymError(status, lib().chym_last_error().decode())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+class Context:
+    """One coupling matrix J and hyperspin dimension D; owns the device run state."""
+
+    def __init__(self, J, D, kind=J_PM1):
+        J = np.ascontiguousarray(J, dtype=np.float64)
+        self.N = int(J.shape[0])
+        self.D = int(D)
+        self.kind = kind
+        h = ctypes.c_void_p()
+        _check(lib().chym_create(_ptr(J), self.N, self.D, int(kind), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().chym_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lambda_max(self):
+        v = ctypes.c_double()
+        _check(lib().chym_lambda_max(self._h, ctypes.byref(v)))
+        return v.value
+
+    def run(self, params: Params, h, seeds, steps, schedule: Schedule, stream=0, n_runs=None):
+        """Host inputs: h (n_h), seeds (n_runs uint64) or None to continue."""
+        h = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+        if seeds is not None:
+            seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+            n_runs = len(seeds)
+        else:
+            n_runs = n_runs if n_runs is not None else self.info()[0]
+        n_h = len(h) if h is not None else self.info()[1]
+        _check(lib().chym_run(self._h, ctypes.byref(params.c()), _ptr(h), n_h, _ptr(seeds),
+                              n_runs, int(steps), ctypes.byref(schedule.c()),
+                              ctypes.c_void_p(stream)))
+
+    def run_device(self, params: Params, d_h, n_h, d_seeds, n_runs, steps, schedule: Schedule,
+                   stream=0):
+        """Device inputs: d_h / d_seeds are device addresses (int), d_seeds 0 to continue."""
+        _check(lib().chym_run_device(self._h, ctypes.byref(params.c()), ctypes.c_void_p(d_h),
+                                     int(n_h), ctypes.c_void_p(d_seeds), int(n_runs), int(steps),
+                                     ctypes.byref(schedule.c()), ctypes.c_void_p(stream)))
+
+    def info(self):
+        n_runs, n_h, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib().chym_info(self._h, ctypes.byref(n_runs), ctypes.byref(n_h), ctypes.byref(k)))
+        return n_runs.value, n_h.value, k.value
+
+    def energy(self, spins=False, stream=0):
+        n_runs = self.info()[0]
+        E = np.zeros(n_runs, dtype=np.float64)
+        S = np.zeros((n_runs, (self.N + 63) // 64), dtype=np.uint64) if spins else None
+        _check(lib().chym_energy(self._h, _ptr(E), _ptr(S), ctypes.c_void_p(stream)))
+        return (E, S) if spins else E
+
+    def energy_device(self, d_E, d_spins=0, stream=0):
+        _check(lib().chym_energy_device(self._h, ctypes.c_void_p(d_E), ctypes.c_void_p(d_spins),
+                                        ctypes.c_void_p(stream)))
+
+    def stats(self, E_gs, n_bins=0, stream=0):
+        n_runs, n_h, _ = self.info()
+        st = CStats()
+        hits = np.zeros(n_h, dtype=np.int64)
+        hist = np.zeros(n_bins, dtype=np.int64) if n_bins else None
+        _check(lib().chym_stats(self._h, float(E_gs), ctypes.byref(st), _ptr(hits), _ptr(hist),
+                                int(n_bins), ctypes.c_void_p(stream)))
+        out = {f: getattr(st, f) for f, _ in CStats._fields_}
+        out["hits"] = hits
+        if hist is not None:
+            out["hist"] = hist
+        return out
+
+    def ground_state_exact(self):
+        """Exact E_GS and minimiser (host, N <= 34)."""
+        e = ctypes.c_double()
+        S = np.zeros((1, (self.N + 63) // 64), dtype=np.uint64)
+        _check(lib().chym_ground_state_exact(self._h, ctypes.byref(e), _ptr(S)))
+        return e.value, unpack_spins(S, self.N)[0]
+
+    def ground_state_search(self, restarts=32, sweeps=1000, seed=1):
+        """Best-known E_GS by simulated annealing (host)."""
+        e = ctypes.c_double()
+        S = np.zeros((1, (self.N + 63) // 64), dtype=np.uint64)
+        _check(lib().chym_ground_state_search(self._h, int(restarts), int(sweeps), int(seed),
+                                              ctypes.byref(e), _ptr(S)))
+        return e.value, unpack_spins(S, self.N)[0]
+
+    def get_state(self, stream=0):
+        n_runs, _, _ = self.info()
+        X = np.zeros((n_runs, self.N, self.D), dtype=np.float64)
+        k = ctypes.c_int64()
+        _check(lib().chym_get_state(self._h, _ptr(X), ctypes.byref(k), ctypes.c_void_p(stream)))
+        return X, k.value
+
+    def set_state(self, X, h, seeds, k, prec, stream=0):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        _check(lib().chym_set_state(self._h, _ptr(X), X.shape[0], _ptr(h), len(h), _ptr(seeds),
+                                    int(k), int(prec), ctypes.c_void_p(stream)))
+
+
+def ground_state_mobius(N, j_ring=-1.0, j_rung=-1.0):
+    """Exact Ising ground-state energy of the Moebius ladder (host)."""
+    e = ctypes.c_double()
+    _check(lib().chym_ground_state_mobius(int(N), float(j_ring), float(j_rung), ctypes.byref(e)))
+    return e.value
+
+
+def unpack_spins(words, N):
+    """Bit-packed spins (bit p of word p // 64 set for +1) to an int8 array of +-1."""
+    words = np.asarray(words, dtype=np.uint64)
+    bits = np.unpackbits(words.view(np.uint8).reshape(words.shape[0], -1), axis=1,
+                         bitorder="little")[:, :N]
+    return (bits.astype(np.int8) * 2 - 1)

@@ -1,0 +1,155 @@
+// chym_internal.cuh -- shared declarations of the CHYM CUDA library.
+//
+// Context layout, error plumbing, the per-step constant block and the device
+// helpers every kernel uses: the Philox4x32-10 generator (Salmon et al., SC'11)
+// and the Box-Muller transform that draw the additive noise of the
+// Euler-Maruyama step, and the dimensional-annealing schedule alpha_mu(k)
+// (C -> alpha_mu C, text after Fig. 2 of arXiv 2308.02329).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/chym.h"
+
+namespace chym {
+
+// ---------------------------------------------------------------- errors ---
+void set_error(const std::string& msg);
+chym_status fail(chym_status st, const std::string& msg);
+chym_status cuda_fail(cudaError_t e, const char* what);
+
+#define CHYM_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return ::chym::cuda_fail(_e, #expr); \
+  } while (0)
+
+// ---------------------------------------------------------- step constants ---
+// Everything a step kernel needs besides pointers.  Built on the host from
+// chym_params / chym_schedule for each chym_run call.
+struct StepConsts {
+  int N, D, n_runs, replicas;
+  int64_t k0, steps;          // first step and number of steps of this launch
+  double dt, noise_scale;     // noise_scale = sigma * sqrt(dt)
+  double gamma, kappa, eps;
+  int sched_kind;             // 0 none, 1 linear
+  int64_t k_anneal, k_total;
+};
+
+// Device status word: bit flags raised by kernels, read back by the host.
+enum : unsigned { STATUS_TIMEOUT = 1u, STATUS_BAD_LAUNCH = 2u };
+
+#if defined(__CUDACC__)
+// ------------------------------------------------------------------ Philox ---
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+// Ten Philox4x32 rounds: two 32x32->64 products, xor with the other half and
+// the round key, key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+// Counter of the noise of spin p, Philox block `blk` (components 4 blk .. 4 blk
+// + 3), stream tag (0 step noise, 1 initial state), step k.
+__device__ __forceinline__ uint4 noise_counter(uint32_t p, uint32_t blk, uint32_t tag,
+                                               uint64_t k) {
+  return make_uint4(p, (tag << 8) | blk, (uint32_t)k, (uint32_t)(k >> 32));
+}
+
+// Box-Muller on one pair of 32-bit words, FP64: u = (w + 1/2) 2^-32,
+// (r cos 2 pi u_a, r sin 2 pi u_a) with r = sqrt(-2 ln u_r).
+__device__ __forceinline__ void box_muller_f64(uint32_t wr, uint32_t wa, double& z0,
+                                               double& z1) {
+  const double ur = ((double)wr + 0.5) * 2.3283064365386963e-10;
+  const double ua = ((double)wa + 0.5) * 2.3283064365386963e-10;
+  const double r = sqrt(-2.0 * log(ur));
+  double s, c;
+  sincospi(2.0 * ua, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// FP32 Box-Muller with the SFU approximations; the angle is taken in
+// (-pi, pi] where the hardware sine/cosine are accurate, and the pair is
+// negated back: cos(t) = -cos(t - pi), sin(t) = -sin(t - pi).  `scale`
+// multiplies both outputs (folded into the radius).
+__device__ __forceinline__ void box_muller_f32(uint32_t wr, uint32_t wa, float scale,
+                                               float& z0, float& z1) {
+  const float ur = __fmaf_rn((float)wr, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float ua = __fmaf_rn((float)wa, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float r = sqrtf(-2.0f * scale * scale * __logf(ur));
+  float s, c;
+  __sincosf(__fmaf_rn(ua, 6.2831853071795865f, -3.1415926535897932f), &s, &c);
+  z0 = -r * c;
+  z1 = -r * s;
+}
+
+// Normal number j (0..3) of a Philox block in FP64.
+__device__ __forceinline__ void block_normals_f64(uint4 w, double z[4]) {
+  box_muller_f64(w.x, w.y, z[0], z[1]);
+  box_muller_f64(w.z, w.w, z[2], z[3]);
+}
+
+#endif  // __CUDACC__
+
+// ------------------------------------------------------- annealing schedule ---
+// alpha_mu(k): 1 for mu = 0 or before k_anneal, then linear down to 0 at k_total.
+__host__ __device__ __forceinline__ double alpha_of(int kind, int64_t k, int64_t k_anneal,
+                                                    int64_t k_total, int mu) {
+  if (kind == 0 || mu == 0 || k < k_anneal) return 1.0;
+  if (k >= k_total) return 0.0;
+  const double a = 1.0 - (double)(k - k_anneal) / (double)(k_total - k_anneal);
+  return a < 0.0 ? 0.0 : a;
+}
+
+}  // namespace chym
+
+// ------------------------------------------------------------------ context ---
+struct chym_ctx {
+  int N = 0, D = 0;
+  chym_jkind kind = CHYM_J_PM1;
+  int device = 0;
+  double* h_J = nullptr;      // host copy, row-major FP64
+  // device copies of J
+  double* d_J64 = nullptr;    // FP64 N x N
+  float* d_J32 = nullptr;     // FP32 N x N
+  int8_t* d_J8 = nullptr;     // int8 N x N (+-1/0 couplings only)
+  void* d_Jbf16 = nullptr;    // BF16, padded for the tensor-core kernels (lazily built)
+  int jbf16_ld = 0;           // leading dimension of d_Jbf16 in elements
+  // batch
+  int n_runs = 0, n_h = 0, cap_runs = 0, cap_h = 0;
+  int64_t k = 0;
+  int32_t prec = -1;          // precision the state is stored in (-1: no state)
+  void* d_X = nullptr;        // state X[run][p][mu], double (FP64) or float
+  size_t x_bytes = 0;
+  double* d_h = nullptr;
+  uint64_t* d_seeds = nullptr;
+  double* d_E = nullptr;      // energies of the last chym_energy*
+  uint64_t* d_spins = nullptr;
+  bool have_energy = false;
+  unsigned* d_status = nullptr;
+  void* d_scratch = nullptr;  // stats scratch
+  size_t scratch_bytes = 0;
+};
+
+namespace chym {
+// kernel launchers (implemented in the .cu files)
+cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_std);
+cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st);
+cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st);
+cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol, double bin_w,
+                         int n_bins, void* d_out, cudaStream_t st);
+double host_lambda_max(const double* J, int N);
+}  // namespace chym

@@ -1,0 +1,227 @@
+// chym_simt.cu -- SIMT step kernels (FP64 checker-comparison mode and the plain
+// FP32 form) and the initial-state kernel.
+//
+// One CTA owns RC runs for the whole launch and keeps their state in shared
+// memory across all steps; J (N x N) is staged in shared memory when it fits
+// and read through L1/L2 otherwise.  Per step:
+//   phase A  y_{p,mu} = sum_q J_pq x_{q,mu}  (C = J_N (x) 1_D, Eq. 1), J symmetric
+//            so thread p reads column p of row q (consecutive p: no bank conflict);
+//            each thread blocks RB runs so one J load feeds RB*D FMAs;
+//   phase B  x <- x + dt [(h-1) x - kappa x^3 - gamma x |x_p|^2 + eps alpha_mu y]
+//            + sigma sqrt(dt) xi  with xi from Philox4x32-10 + Box-Muller.
+#include <algorithm>
+
+#include "chym_internal.cuh"
+
+namespace chym {
+namespace {
+
+template <typename T>
+struct SimtTraits;
+template <>
+struct SimtTraits<double> {
+  static constexpr int RB = 1;
+};
+template <>
+struct SimtTraits<float> {
+  static constexpr int RB = 4;
+};
+
+// Normal numbers of spin p for components 0..D-1 at step k (tag 0 or 1).
+template <typename T, int D>
+__device__ __forceinline__ void spin_normals(uint64_t seed, uint32_t tag, uint64_t k, int p,
+                                             T scale, T z[D]) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+    const uint4 w = philox4x32_10(noise_counter((uint32_t)p, (uint32_t)blk, tag, k), k0, k1);
+    T zz[4];
+    if constexpr (sizeof(T) == 8) {
+      double d[4];
+      box_muller_f64(w.x, w.y, d[0], d[1]);
+      if (D - 4 * blk > 2) box_muller_f64(w.z, w.w, d[2], d[3]);
+      else d[2] = d[3] = 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) zz[j] = (T)(d[j] * (double)scale);
+    } else {
+      box_muller_f32(w.x, w.y, (float)scale, zz[0], zz[1]);
+      if (D - 4 * blk > 2) box_muller_f32(w.z, w.w, (float)scale, zz[2], zz[3]);
+      else zz[2] = zz[3] = 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (4 * blk + j < D) z[4 * blk + j] = zz[j];
+  }
+}
+
+template <typename T, int D>
+__global__ void init_kernel(T* __restrict__ X, const uint64_t* __restrict__ seeds, int N,
+                            int n_runs, T init_std) {
+  const int64_t pairs = (int64_t)N * n_runs;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < pairs;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int run = (int)(s / N), p = (int)(s % N);
+    T z[D];
+    spin_normals<T, D>(seeds[run], 1u, 0ull, p, init_std, z);
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) X[s * D + mu] = z[mu];
+  }
+}
+
+template <typename T, int D, bool J_SMEM>
+__global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg,
+                                                        T* __restrict__ Xg,
+                                                        const double* __restrict__ hg,
+                                                        const uint64_t* __restrict__ seeds,
+                                                        StepConsts sc, int RC) {
+  constexpr int RB = SimtTraits<T>::RB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = sc.N;
+  T* Js = reinterpret_cast<T*>(smem_raw);
+  T* Xs = J_SMEM ? Js + (size_t)N * N : Js;
+  T* Ys = Xs + (size_t)RC * N * D;
+  const int run0 = blockIdx.x * RC;
+  const int nr = min(RC, sc.n_runs - run0);
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  if (J_SMEM)
+    for (int i = tid; i < N * N; i += nt) Js[i] = Jg[i];
+  for (int i = tid; i < RC * N * D; i += nt)
+    Xs[i] = (i < nr * N * D) ? Xg[(size_t)run0 * N * D + i] : T(0);
+  __syncthreads();
+  const T* Jsrc = J_SMEM ? Js : Jg;
+
+  const T dt = (T)sc.dt, gamma = (T)sc.gamma, kappa = (T)sc.kappa;
+  const int n_groups = RC / RB;
+  for (int64_t k = sc.k0; k < sc.k0 + sc.steps; ++k) {
+    // ---- phase A: coupling product, RB runs per thread ----
+    for (int slot = tid; slot < N * n_groups; slot += nt) {
+      const int p = slot % N, g = slot / N;
+      T acc[RB][D];
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) acc[b][mu] = T(0);
+      const T* xg = Xs + (size_t)(g * RB) * N * D;
+      for (int q = 0; q < N; ++q) {
+        const T j = J_SMEM ? Jsrc[q * N + p] : __ldg(Jsrc + (size_t)q * N + p);
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) acc[b][mu] = fma(j, xg[((size_t)b * N + q) * D + mu], acc[b][mu]);
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) Ys[((size_t)(g * RB + b) * N + p) * D + mu] = acc[b][mu];
+    }
+    __syncthreads();
+    // ---- phase B: local drift, annealing and noise ----
+    T ea[D];
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu)
+      ea[mu] = (T)(sc.eps * alpha_of(sc.sched_kind, k, sc.k_anneal, sc.k_total, mu));
+    for (int s = tid; s < nr * N; s += nt) {
+      const int rl = s / N, p = s % N, run = run0 + rl;
+      const T hm1 = (T)(hg[run / sc.replicas] - 1.0);
+      T* x = Xs + (size_t)s * D;
+      const T* y = Ys + (size_t)s * D;
+      T n2 = T(0);
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) n2 = fma(x[mu], x[mu], n2);
+      T z[D];
+      spin_normals<T, D>(seeds[run], 0u, (uint64_t)k, p, (T)sc.noise_scale, z);
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) {
+        const T xm = x[mu];
+        const T f = hm1 * xm - kappa * xm * xm * xm - gamma * xm * n2 + ea[mu] * y[mu];
+        x[mu] = xm + dt * f + z[mu];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nr * N * D; i += nt) Xg[(size_t)run0 * N * D + i] = Xs[i];
+}
+
+template <typename T, int D>
+cudaError_t launch_simt_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
+  constexpr int RB = SimtTraits<T>::RB;
+  const int N = c->N;
+  const size_t budget = 200 * 1024;
+  const size_t j_bytes = (size_t)N * N * sizeof(T);
+  const bool j_smem = j_bytes <= budget / 2;
+  const size_t per_run = (size_t)2 * N * D * sizeof(T);
+  const size_t avail = budget - (j_smem ? j_bytes : 0);
+  int RC = (int)std::min<size_t>(avail / per_run, 64);
+  RC = std::max(RB, RC / RB * RB);
+  if ((size_t)RC * per_run > avail) return cudaErrorInvalidConfiguration;  // N too large
+  // do not make CTAs larger than needed to fill the GPU
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  while (RC > RB && (int64_t)((sc.n_runs + RC - 1) / RC) < sms) RC -= RB;
+  const size_t smem = (j_smem ? j_bytes : 0) + (size_t)RC * per_run;
+  const int threads = std::min(512, std::max(64, ((N * (RC / RB) + 31) / 32) * 32));
+  const int grid = (sc.n_runs + RC - 1) / RC;
+  const T* J = sizeof(T) == 8 ? (const T*)c->d_J64 : (const T*)c->d_J32;
+  T* X = (T*)c->d_X;
+  if (j_smem) {
+    auto kern = step_simt_kernel<T, D, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, threads, smem, st>>>(J, X, c->d_h, c->d_seeds, sc, RC);
+  } else {
+    auto kern = step_simt_kernel<T, D, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, threads, smem, st>>>(J, X, c->d_h, c->d_seeds, sc, RC);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_simt_D(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
+  switch (c->D) {
+    case 1: return launch_simt_typed<T, 1>(c, sc, st);
+    case 2: return launch_simt_typed<T, 2>(c, sc, st);
+    case 3: return launch_simt_typed<T, 3>(c, sc, st);
+    case 4: return launch_simt_typed<T, 4>(c, sc, st);
+    case 5: return launch_simt_typed<T, 5>(c, sc, st);
+    case 6: return launch_simt_typed<T, 6>(c, sc, st);
+    case 7: return launch_simt_typed<T, 7>(c, sc, st);
+    case 8: return launch_simt_typed<T, 8>(c, sc, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_init_typed(chym_ctx* c, cudaStream_t st, double init_std) {
+  const int64_t pairs = (int64_t)c->N * c->n_runs;
+  const int threads = 256;
+  const int grid = (int)std::min<int64_t>((pairs + threads - 1) / threads, 152 * 32);
+  T* X = (T*)c->d_X;
+  switch (c->D) {
+#define CHYM_INIT_CASE(DD) \
+  case DD: init_kernel<T, DD><<<grid, threads, 0, st>>>(X, c->d_seeds, c->N, c->n_runs, (T)init_std); break;
+    CHYM_INIT_CASE(1) CHYM_INIT_CASE(2) CHYM_INIT_CASE(3) CHYM_INIT_CASE(4)
+    CHYM_INIT_CASE(5) CHYM_INIT_CASE(6) CHYM_INIT_CASE(7) CHYM_INIT_CASE(8)
+#undef CHYM_INIT_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st) {
+  if (sc.steps <= 0 || sc.n_runs <= 0) return cudaSuccess;
+  if (prec == CHYM_PREC_FP64) return launch_simt_D<double>(c, sc, st);
+  return launch_simt_D<float>(c, sc, st);
+}
+
+cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_std) {
+  if (c->n_runs <= 0) return cudaSuccess;
+  if (prec == CHYM_PREC_FP64) return launch_init_typed<double>(c, st, init_std);
+  return launch_init_typed<float>(c, st, init_std);
+}
+
+}  // namespace chym

@@ -1,0 +1,241 @@
+"""GPU parity of the CUDA path against the FP64 CPU checker, through the C ABI.
+
+Tolerances (written here, derived from the arithmetic):
+  * FP64 mode: state and per-step right-hand side within 1e-10 relative;
+  * FP32 mode: state within 1e-4 relative over short horizons;
+  * Ising spins and energies: bit-exact (integers), compared where the
+    surviving component is not within rounding of zero.
+"""
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from oracle.stats import figures_of_merit, energy_histogram
+from paper_2308_02329_gb300 import chym, inputs
+from tests.helpers import make_case, oracle_params, oracle_schedule
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    chym.lib()
+
+
+def _rel_err(a, b):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return np.max(np.abs(a - b)) / scale
+
+
+def _run_both(N, D, n_h, reps, steps, prec, graph="sk", sched_kind=1, seed=7, kappa=0.1,
+              sigma=1e-3):
+    J, eps, h, seeds = make_case(N, D, n_h, reps, seed, graph)
+    kind = chym.J_REAL if graph == "gauss" else chym.J_PM1
+    ctx = chym.Context(J, D, kind)
+    prm = chym.Params(eps=eps, prec=prec, kappa=kappa, sigma=sigma)
+    sch = chym.Schedule(sched_kind, steps // 2 if sched_kind else 0, max(steps, 1))
+    ctx.run(prm, h, seeds, steps, sch)
+    X, k = ctx.get_state()
+    assert k == steps
+    Xo = O.run(J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm), oracle_schedule(sch),
+               steps)
+    return ctx, J, X, Xo
+
+
+FP64_CASES = [
+    # N, D, n_h, reps, steps, graph
+    (1, 1, 1, 3, 20, "sk"),
+    (3, 2, 2, 3, 30, "sk"),
+    (20, 3, 8, 4, 60, "sk"),         # 3000-step workload's shape, short horizon
+    (37, 8, 3, 7, 25, "sparse"),     # ragged N, two Philox blocks per spin
+    (100, 4, 4, 5, 40, "mobius"),
+    (100, 2, 2, 3, 40, "sk"),
+    (130, 5, 2, 2, 20, "gauss"),     # J larger than the shared-memory budget
+]
+
+
+@pytest.mark.parametrize("N,D,n_h,reps,steps,graph", FP64_CASES)
+def test_fp64_state_matches_checker(N, D, n_h, reps, steps, graph):
+    ctx, J, X, Xo = _run_both(N, D, n_h, reps, steps, chym.PREC_FP64, graph)
+    assert _rel_err(X, Xo) <= 1e-10
+    ctx.close()
+
+
+def test_fp64_zero_steps_is_the_initial_state():
+    ctx, J, X, Xo = _run_both(17, 3, 2, 5, 0, chym.PREC_FP64)
+    assert _rel_err(X, Xo) <= 1e-15
+    ctx.close()
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 8])
+def test_fp64_one_step_rhs(D):
+    """Per-step right-hand side f(x) within 1e-10 relative, from an arbitrary state."""
+    N, n_h, reps = 29, 3, 3
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 11)
+    rng = np.random.default_rng(D)
+    X0 = 0.2 * rng.standard_normal((n_h * reps, N, D))
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=chym.PREC_FP64, sigma=0.0, kappa=0.3)
+    sch = chym.Schedule(1, 5, 20)
+    for k0 in (0, 12):  # before and during the annealing ramp
+        ctx.set_state(X0, h, seeds, k0, chym.PREC_FP64)
+        ctx.run(prm, None, None, 1, sch, n_runs=len(seeds))
+        X1, k = ctx.get_state()
+        assert k == k0 + 1
+        f_gpu = (X1 - X0) / prm.dt
+        hr = inputs.h_per_run(h, reps)
+        f_or = np.stack([O.drift(J, X0[r], hr[r], oracle_params(prm), oracle_schedule(sch), k0)
+                         for r in range(len(seeds))])
+        assert _rel_err(f_gpu, f_or) <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("N,D,steps", [(20, 3, 60), (100, 4, 40), (64, 2, 50), (45, 8, 30)])
+def test_fp32_state_matches_checker(N, D, steps):
+    ctx, J, X, Xo = _run_both(N, D, 4, 5, steps, chym.PREC_FP32)
+    assert _rel_err(X, Xo) <= 1e-4
+    ctx.close()
+
+
+def _comparable(X, thresh=1e-7):
+    return np.abs(X[..., 0]) > thresh
+
+
+@pytest.mark.parametrize("graph,prec", [("sk", chym.PREC_FP64), ("mobius", chym.PREC_FP32),
+                                        ("gauss", chym.PREC_FP64)])
+def test_spins_and_energies(graph, prec):
+    N, D = 60, 3
+    ctx, J, X, Xo = _run_both(N, D, 4, 8, 200, prec, graph)
+    E, S = ctx.energy(spins=True)
+    s_gpu = chym.unpack_spins(S, N)
+    # the readout of the GPU's own state is exact
+    assert np.array_equal(s_gpu, O.readout(X))
+    Eo = O.ising_energies(J, s_gpu)
+    if graph == "gauss":
+        np.testing.assert_allclose(E, Eo, rtol=1e-12, atol=1e-12)
+    else:
+        assert np.array_equal(E, Eo)
+        # every +-1 energy obeys E = -sum J (mod 4)
+        assert np.all((E + J.sum()) % 4 == 0)
+    # same trajectories: spins agree wherever the component is not at rounding level
+    mask = _comparable(Xo, 1e-6)
+    assert np.array_equal(np.sign(X[..., 0])[mask] >= 0, np.sign(Xo[..., 0])[mask] >= 0)
+    ctx.close()
+
+
+def test_checkpoint_resume_is_bit_identical():
+    N, D, n_h, reps, K = 40, 4, 2, 4, 120
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 3)
+    prm = chym.Params(eps=eps, prec=chym.PREC_FP64)
+    sch = chym.Schedule(1, 50, K)
+    a = chym.Context(J, D)
+    a.run(prm, h, seeds, K, sch)
+    Xa, _ = a.get_state()
+    b = chym.Context(J, D)
+    b.run(prm, h, seeds, K // 3, sch)
+    Xb, kb = b.get_state()
+    b.set_state(Xb, h, seeds, kb, chym.PREC_FP64)   # round trip through a host checkpoint
+    b.run(prm, None, None, K - K // 3, sch, n_runs=len(seeds))
+    Xc, kc = b.get_state()
+    assert kc == K and np.array_equal(Xa, Xc)
+    a.close()
+    b.close()
+
+
+def test_stats_match_checker_figures_of_merit():
+    N, D, n_h, reps = 16, 2, 4, 16
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 5)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=chym.PREC_FP64)
+    ctx.run(prm, h, seeds, 1500, chym.Schedule(1, 750, 1500))
+    E = ctx.energy()
+    E_gs, _ = O.ground_state_bruteforce(J)
+    st = ctx.stats(E_gs, n_bins=64)
+    fm = figures_of_merit(E, E_gs, n_h)
+    assert st["hits"].tolist() == fm["hits"].tolist()
+    assert st["P_max"] == fm["P_max"]
+    assert st["W_range"] == pytest.approx(fm["W_range"], abs=1e-15)
+    assert st["W_scan"] == pytest.approx(fm["W_scan"], abs=1e-15)
+    assert st["dE_mean"] == pytest.approx(fm["dE_mean"], rel=1e-12, abs=1e-12)
+    assert st["best_E"] == E.min() and st["best_run"] == int(np.argmin(E))
+    assert st["n_finite"] == len(E) and st["n_hits"] == fm["hits"].sum()
+    lv, ct = energy_histogram(E)
+    hist = np.zeros(64, dtype=np.int64)
+    for l, c in zip(lv, ct):
+        hist[min(int(round((l - E_gs) / 4)), 63)] += c
+    assert st["hist"].tolist() == hist.tolist()
+    ctx.close()
+
+
+def test_statistical_parity_fp64_full_horizon():
+    """SK +-1 N=20, D=3, 8 pumps x 32 replicas, 3000 steps (1500 + 1500 annealing):
+    P_Ising(h) of the GPU and of the checker agree within binomial 95% intervals, and the
+    ground state is the brute-force one."""
+    N, D, n_h, reps, K = 20, 3, 8, 32, 3000
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 0xC0FFEE)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=chym.PREC_FP64)
+    sch = chym.Schedule(1, 1500, K)
+    ctx.run(prm, h, seeds, K, sch)
+    E = ctx.energy()
+    Xo = O.run(J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm), oracle_schedule(sch), K)
+    Eo = O.ising_energies(J, O.readout(Xo))
+    E_gs, _ = O.ground_state_bruteforce(J)
+    assert E.min() >= E_gs
+    P = (E.reshape(n_h, reps) == E_gs).mean(1)
+    Po = (Eo.reshape(n_h, reps) == E_gs).mean(1)
+    for p, q in zip(P, Po):
+        half = 1.96 * np.sqrt(max(p * (1 - p), q * (1 - q), 1.0 / reps) * 2.0 / reps)
+        assert abs(p - q) <= half + 1e-12
+    # FP64 on both sides: the large majority of runs end in the very same state
+    assert np.mean(E == Eo) >= 0.9
+    ctx.close()
+
+
+def test_invalid_arguments_and_order():
+    J, eps, h, seeds = make_case(10, 2, 2, 3, 1)
+    ctx = chym.Context(J, 2)
+    prm = chym.Params(eps=eps, prec=chym.PREC_FP64)
+    with pytest.raises(chym.ChymError) as e:
+        ctx.energy()
+    assert e.value.status == chym.ESTATE
+    with pytest.raises(chym.ChymError) as e:
+        ctx.run(prm, h, seeds[:5], 10, chym.Schedule(0, 0, 1))  # 5 runs, 2 pumps
+    assert e.value.status == chym.EINVAL
+    with pytest.raises(chym.ChymError) as e:
+        ctx.run(prm, h, seeds, 10, chym.Schedule(1, 10, 5))     # k_total <= k_anneal
+    assert e.value.status == chym.EINVAL
+    ctx.run(prm, h, seeds, 10, chym.Schedule(0, 0, 1))
+    with pytest.raises(chym.ChymError) as e:
+        ctx.run(chym.Params(eps=eps, prec=chym.PREC_FP32), None, None, 5, chym.Schedule(0, 0, 1),
+                n_runs=len(seeds))
+    assert e.value.status == chym.EINVAL
+    bad = chym.Params(eps=eps, prec=chym.PREC_FP64, dt=-1.0)
+    with pytest.raises(chym.ChymError) as e:
+        ctx.run(bad, h, seeds, 10, chym.Schedule(0, 0, 1))
+    assert e.value.status == chym.EINVAL
+    ctx.close()
+
+
+def test_lambda_max_matches_eigvalsh():
+    for J in (inputs.sk_pm1(50, 2), inputs.mobius_ladder(40), inputs.gaussian(70, 3)):
+        ctx = chym.Context(J, 1, chym.J_REAL)
+        assert ctx.lambda_max() == pytest.approx(np.linalg.eigvalsh(J)[-1], rel=1e-10)
+        ctx.close()
+
+
+def test_ground_state_references_match_checker():
+    for N, seed in ((8, 1), (14, 2), (20, 0xC0FFEE)):
+        J = inputs.sk_pm1(N, seed)
+        ctx = chym.Context(J, 1)
+        e, s = ctx.ground_state_exact()
+        assert e == O.ground_state_bruteforce(J)[0]
+        assert O.ising_energy(J, s) == e
+        e_sa, s_sa = ctx.ground_state_search(restarts=16, sweeps=300, seed=3)
+        assert e_sa >= e and O.ising_energy(J, s_sa) == e_sa
+        ctx.close()
+    for N in (6, 10, 20, 100):
+        assert chym.ground_state_mobius(N) == O.ground_state_mobius(N, -1.0, -1.0)
