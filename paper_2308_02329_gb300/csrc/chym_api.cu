@@ -138,6 +138,18 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
   return CHYM_OK;
 }
 
+// Read and clear the device status word after the stream has been synchronised.
+chym_status check_device_status(chym_ctx* c) {
+  unsigned st = 0;
+  CHYM_CUDA_TRY(cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st) {
+    CHYM_CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+    if (st & STATUS_TIMEOUT) return fail(CHYM_ETIMEOUT, "a device-side wait timed out; state not updated");
+    return fail(CHYM_ECUDA, "device status word set");
+  }
+  return CHYM_OK;
+}
+
 chym_status check_run_args(chym_ctx* c, const chym_params* prm, int n_h, int n_runs,
                            int64_t steps, const chym_schedule* sched, bool have_seeds) {
   if (!c) return fail(CHYM_EINVAL, "ctx is NULL");
@@ -160,6 +172,7 @@ chym_status check_run_args(chym_ctx* c, const chym_params* prm, int n_h, int n_r
 
 cudaError_t launch_step(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st) {
   if (prec == CHYM_PREC_FP64 || prec == CHYM_PREC_FP32) return launch_step_simt(c, sc, prec, st);
+  if (prec == CHYM_PREC_BF16X2) return launch_step_tc(c, sc, st);
   return cudaErrorNotSupported;
 }
 
@@ -322,7 +335,7 @@ chym_status chym_energy(chym_ctx* c, double* E_out, uint64_t* spins_out, void* s
                                   cudaMemcpyDeviceToHost, st));
   }
   CHYM_CUDA_TRY(cudaStreamSynchronize(st));
-  return CHYM_OK;
+  return check_device_status(c);
 }
 
 chym_status chym_stats(chym_ctx* c, double E_gs, chym_stats_t* out, int64_t* hits_per_h,
@@ -393,7 +406,7 @@ chym_status chym_get_state(chym_ctx* c, double* X_out, int64_t* k_out, void* str
     for (size_t i = 0; i < n; ++i) X_out[i] = tmp[i];
   }
   if (k_out) *k_out = c->k;
-  return CHYM_OK;
+  return check_device_status(c);
 }
 
 chym_status chym_set_state(chym_ctx* c, const double* X, int n_runs, const double* h, int n_h,

@@ -148,6 +148,7 @@ namespace chym {
 // kernel launchers (implemented in the .cu files)
 cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_std);
 cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st);
+cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st);
 cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol, double bin_w,
                          int n_bins, void* d_out, cudaStream_t st);

@@ -1,0 +1,520 @@
+// chym_tc.cu -- fused tensor-core step kernel for N <= 128 (BF16 hi+lo coupling,
+// FP32 state), persistent over all steps of a launch.
+//
+// Per step, for every group of runs (one warpgroup of 128 threads, thread = spin
+// p = TMEM lane):
+//   1. one thread issues tcgen05.mma:  Y (128 x C, FP32 in TMEM) =
+//        J_hi X_hi + J_hi X_lo (+ J_lo X_hi for real J)            (C = J_N (x) 1_D, Eq. 1)
+//      A = J (BF16, K-major canonical layout, staged once by a TMA bulk copy),
+//      B = X split into BF16 hi + lo (MN-major canonical layout in shared memory),
+//      columns ordered c = mu * R + r so a thread's 8 consecutive runs of one
+//      component are 8 consecutive columns;
+//   2. the warpgroup reads its rows of Y (tcgen05.ld) and the FP32 master state
+//      (kept in TMEM beside the accumulator), applies the local drift, the
+//      non-local loss, the annealing scale alpha_mu(k) (text after Fig. 2) and the
+//      Philox4x32-10 / Box-Muller noise:
+//        x <- x (1 + dt(h-1) - dt gamma |x_p|^2 - dt kappa x^2) + dt eps alpha_mu y
+//             + sigma sqrt(dt) xi,
+//      writes x back to TMEM and its BF16 hi/lo split into the B operand.
+// Up to four groups share an SM and interleave their tensor-core and ALU phases.
+// Every wait is bounded (%globaltimer); on timeout the kernel raises a status bit,
+// drains its own tensor-core work with another bounded wait, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "chym_internal.cuh"
+
+namespace chym {
+namespace {
+
+struct TcArgs {
+  int N, KP, n_runs, replicas, G, a_terms;
+  int64_t k0, steps;
+  float dt, noise_scale, gdt, kdt, edt, inv_ramp;
+  int sched_kind;
+  int64_t k_anneal, k_total;
+  unsigned* status;
+};
+
+template <int D>
+struct TcCfg {
+  static constexpr int RG = D == 1 ? 64 : D == 2 ? 32 : (D == 6 || D == 8) ? 8 : 16;
+  static constexpr int CG = D * RG;        // MMA N: columns of one group
+  static constexpr int CH = D <= 4 ? 8 : 4;  // runs per epilogue chunk
+  static constexpr int G = std::min(4, 512 / (2 * CG));
+  static_assert(CG % 16 == 0 && CG <= 256, "MMA N must be a multiple of 16 in [16, 256]");
+  static_assert(RG % CH == 0, "chunk must divide the group");
+};
+
+constexpr int kTimeoutNs = 2000000000;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255u) == 0u) {
+      const uint64_t t = global_timer();
+      if (it == 0) t0 = t;
+      else if (t - t0 > (uint64_t)kTimeoutNs) return false;
+    }
+  }
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, byte offset between
+// core matrices along K (lbo) and along M/N (sbo), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+template <int CH>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[CH]) {
+  if constexpr (CH == 8) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+  } else {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+  }
+}
+
+template <int CH>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const float (&v)[CH]) {
+  if constexpr (CH == 8) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
+  } else {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                 "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])));
+  }
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Named barrier of one warpgroup; returns the OR of `flag` over its 128 threads.
+__device__ __forceinline__ int group_bar_or(int id, int flag) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, 128, p;\n\tselp.s32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"(flag), "r"(id)
+      : "memory");
+  return r;
+}
+
+// Split 2*n FP32 values into packed BF16 hi words and BF16 lo words (lo = x - hi).
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+  const float ah = __low2float(h2), bh = __high2float(h2);
+  const __nv_bfloat162 l2 = __floats2bfloat162_rn(a - ah, b - bh);
+  hi = *reinterpret_cast<const uint32_t*>(&h2);
+  lo = *reinterpret_cast<const uint32_t*>(&l2);
+}
+
+// Write CH consecutive B columns (n0 .. n0+CH-1) of row k = spin p, hi and lo.
+template <int CH>
+__device__ __forceinline__ void store_b(uint8_t* Bhi, uint8_t* Blo, uint32_t off, const float (&v)[CH]) {
+  uint32_t h[CH / 2], l[CH / 2];
+#pragma unroll
+  for (int j = 0; j < CH / 2; ++j) split_pair(v[2 * j], v[2 * j + 1], h[j], l[j]);
+  if constexpr (CH == 8) {
+    *reinterpret_cast<uint4*>(Bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(Blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  } else {
+    *reinterpret_cast<uint2*>(Bhi + off) = make_uint2(h[0], h[1]);
+    *reinterpret_cast<uint2*>(Blo + off) = make_uint2(l[0], l[1]);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restrict__ Aimg,
+                                                         float* __restrict__ X,
+                                                         const double* __restrict__ hg,
+                                                         const uint64_t* __restrict__ seeds,
+                                                         TcArgs a) {
+  using Cfg = TcCfg<D>;
+  constexpr int RG = Cfg::RG, CG = Cfg::CG, CH = Cfg::CH, G = Cfg::G;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ __align__(8) uint64_t s_mbar[G];
+  __shared__ __align__(8) uint64_t s_abar;
+  __shared__ float s_ar[G][RG];
+  __shared__ uint2 s_key[G][RG];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp >> 2, wq = warp & 3;
+  const int p = wq * 32 + lane;  // spin = TMEM lane
+  const int N = a.N, KP = a.KP;
+  const uint32_t a_bytes = 128u * (uint32_t)KP * 2u;
+  const uint32_t b_bytes = (uint32_t)KP * CG * 2u;
+  uint8_t* Bhi = smem + a.a_terms * a_bytes + (size_t)g * 2 * b_bytes;
+  uint8_t* Blo = Bhi + b_bytes;
+  const uint32_t lbo_b = (CG / 8) * 128u;  // B: core-matrix stride along K
+  const int run0 = (blockIdx.x * G + g) * RG;
+  const int nr = max(0, min(RG, a.n_runs - run0));
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&s_tmem)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_abar)));
+    for (int q = 0; q < G; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[q])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // per-run constants of this group: 1 + dt (h - 1) and the Philox key
+  if (p < RG) {
+    const int run = run0 + p;
+    float ar = 0.f;
+    uint2 key = make_uint2(0u, 0u);
+    if (p < nr) {
+      ar = (float)(1.0 + (double)a.dt * (hg[run / a.replicas] - 1.0));
+      const uint64_t s = seeds[run];
+      key = make_uint2((uint32_t)s, (uint32_t)(s >> 32));
+    }
+    s_ar[g][p] = ar;
+    s_key[g][p] = key;
+  }
+  // zero the B operands (K padding rows must stay finite zeros)
+  for (uint32_t o = (uint32_t)(tid & 127) * 16u; o < 2u * b_bytes; o += 128u * 16u)
+    *reinterpret_cast<uint4*>(Bhi + o) = make_uint4(0u, 0u, 0u, 0u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) {  // TMA bulk copy of the prepared J image (all terms)
+    const uint32_t bytes = (uint32_t)a.a_terms * a_bytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&s_abar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(smem)),
+        "l"(Aimg), "r"(bytes), "r"(smem_addr(&s_abar))
+        : "memory");
+  }
+  const uint32_t tmem = s_tmem;
+  const uint32_t t_lane = tmem + ((uint32_t)(wq * 32) << 16);
+  const uint32_t acc_col = (uint32_t)(g * CG);
+  const uint32_t mst_col = (uint32_t)(G * CG + g * CG);
+  // B store offset of row k = p: (p % 8) * 16 + (p / 8) * lbo_b; column block adds n0/8*128 + n0%8*2
+  const uint32_t b_row_off = (uint32_t)(p & 7) * 16u + (uint32_t)(p >> 3) * lbo_b;
+  const bool live = p < N;
+
+  // ---- load the state: X[run][p][mu] -> TMEM master + BF16 hi/lo B ----
+  if (nr > 0) {
+    for (int r0 = 0; r0 < RG; r0 += CH) {
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) {
+        float v[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int r = r0 + j;
+          v[j] = (live && r < nr) ? X[((size_t)(run0 + r) * N + p) * D + mu] : 0.f;
+        }
+        tmem_st<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), v);
+        const uint32_t n0 = (uint32_t)(mu * RG + r0);
+        if (live) store_b<CH>(Bhi, Blo, b_row_off + (n0 >> 3) * 128u + (n0 & 7u) * 2u, v);
+      }
+    }
+  }
+  tmem_wait_st();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+
+  // ---- step loop (each group independently) ----
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
+                         ((uint32_t)(CG >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const uint32_t a_sbo = (uint32_t)(KP / 8) * 128u;
+  const uint32_t a_base = smem_addr(smem);
+  const uint32_t bhi_base = smem_addr(Bhi), blo_base = smem_addr(Blo);
+  const int ksteps = KP / 16;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  if (nr > 0) {
+    for (int64_t k = a.k0; k < a.k0 + a.steps; ++k) {
+      if (wq == 0 && lane == 0) {
+        bool ok = true;
+        if (k == a.k0) ok = mbar_wait(smem_addr(&s_abar), 0);
+        tc_fence_after();
+        if (ok) {
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
+            mma_bf16(tmem + acc_col, da, smem_desc(bhi_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
+                     idesc, ks > 0);
+          }
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
+            mma_bf16(tmem + acc_col, da, smem_desc(blo_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
+                     idesc, 1u);
+          }
+          if (a.a_terms > 1) {
+            for (int ks = 0; ks < ksteps; ++ks) {
+              const uint64_t da = smem_desc(a_base + a_bytes + (uint32_t)ks * 256u, 128u, a_sbo);
+              mma_bf16(tmem + acc_col, da, smem_desc(bhi_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
+                       idesc, 1u);
+            }
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_addr(&s_mbar[g]))
+              : "memory");
+        } else {
+          atomicOr(a.status, STATUS_TIMEOUT);
+          s_abort = 1;
+          // nothing was issued: complete the phase so the group does not wait
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_mbar[g])) : "memory");
+        }
+      }
+      // warp-uniform outcome: the TMEM loads below are warp-collective
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&s_mbar[g]), phase));
+      phase ^= 1u;
+      if (!ok) {
+        timed_out = true;
+        atomicOr(a.status, STATUS_TIMEOUT);
+        s_abort = 1;
+      }
+      tc_fence_after();
+      // per-step coupling scale dt eps alpha_mu(k)
+      float e_mu[D];
+      {
+        float ramp = 1.f;
+        if (a.sched_kind == 1 && k >= a.k_anneal)
+          ramp = k >= a.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(k - a.k_anneal) * a.inv_ramp);
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) e_mu[mu] = a.edt * (mu == 0 ? 1.f : ramp);
+      }
+      if (ok) {
+        for (int r0 = 0; r0 < RG; r0 += CH) {
+          float x[D][CH], y[D][CH];
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) {
+            tmem_ld<CH>(t_lane + acc_col + (uint32_t)(mu * RG + r0), y[mu]);
+            tmem_ld<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), x[mu]);
+          }
+          tmem_wait_ld();
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+              const int r = r0 + j;
+              const float ar = s_ar[g][r];
+              const uint2 key = s_key[g][r];
+              float n2 = 0.f;
+#pragma unroll
+              for (int mu = 0; mu < D; ++mu) n2 = fmaf(x[mu][j], x[mu][j], n2);
+              const float t = fmaf(-a.gdt, n2, ar);
+              float z[4 * ((D + 3) / 4)];
+#pragma unroll
+              for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+                const uint4 w = philox4x32_10(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)k),
+                                              key.x, key.y);
+                box_muller_f32(w.x, w.y, a.noise_scale, z[4 * blk], z[4 * blk + 1]);
+                if (D - 4 * blk > 2) box_muller_f32(w.z, w.w, a.noise_scale, z[4 * blk + 2], z[4 * blk + 3]);
+                else z[4 * blk + 2] = z[4 * blk + 3] = 0.f;
+              }
+#pragma unroll
+              for (int mu = 0; mu < D; ++mu) {
+                const float xm = x[mu][j];
+                const float s = fmaf(-a.kdt * xm, xm, t);
+                x[mu][j] = fmaf(xm, s, fmaf(e_mu[mu], y[mu][j], z[mu]));
+              }
+            }
+          }
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) {
+            tmem_st<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), x[mu]);
+            const uint32_t n0 = (uint32_t)(mu * RG + r0);
+            if (live) store_b<CH>(Bhi, Blo, b_row_off + (n0 >> 3) * 128u + (n0 & 7u) * 2u, x[mu]);
+          }
+        }
+      }
+      tmem_wait_st();
+      fence_async_smem();
+      tc_fence_before();
+      if (group_bar_or(1 + g, s_abort)) break;
+    }
+  }
+  if (timed_out && wq == 0 && lane == 0) {
+    // the tensor core may still own this group's accumulator: wait once more (bounded)
+    mbar_wait(smem_addr(&s_mbar[g]), phase ^ 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const bool aborted = s_abort != 0;
+  // ---- store the state back (skipped after a timeout: the status reports it) ----
+  if (nr > 0 && !aborted) {
+    for (int r0 = 0; r0 < RG; r0 += CH) {
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) {
+        float v[CH];
+        tmem_ld<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), v);
+        tmem_wait_ld();
+        if (live) {
+#pragma unroll
+          for (int j = 0; j < CH; ++j)
+            if (r0 + j < nr) X[((size_t)(run0 + r0 + j) * N + p) * D + mu] = v[j];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// Host: IEEE round-to-nearest-even of an FP32 value to BF16 (bit pattern).
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)((u >> 16) | ((u & 0xFFFFu) ? 0x40u : 0u));
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7FFFu + lsb;
+  return (uint16_t)(u >> 16);
+}
+float bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+template <int D>
+cudaError_t launch_tc_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
+  using Cfg = TcCfg<D>;
+  const int KP = (c->N + 15) / 16 * 16;
+  const int a_terms = c->kind == CHYM_J_PM1 ? 1 : 2;
+  TcArgs a;
+  a.N = c->N;
+  a.KP = KP;
+  a.n_runs = sc.n_runs;
+  a.replicas = sc.replicas;
+  a.G = Cfg::G;
+  a.a_terms = a_terms;
+  a.k0 = sc.k0;
+  a.steps = sc.steps;
+  a.dt = (float)sc.dt;
+  a.noise_scale = (float)sc.noise_scale;
+  a.gdt = (float)(sc.dt * sc.gamma);
+  a.kdt = (float)(sc.dt * sc.kappa);
+  a.edt = (float)(sc.dt * sc.eps);
+  a.sched_kind = sc.sched_kind;
+  a.k_anneal = sc.k_anneal;
+  a.k_total = sc.k_total;
+  a.inv_ramp = sc.sched_kind == 1 ? (float)(1.0 / (double)(sc.k_total - sc.k_anneal)) : 0.f;
+  a.status = c->d_status;
+  const size_t a_bytes = 128u * (size_t)KP * 2u;
+  const size_t b_bytes = (size_t)KP * Cfg::CG * 2u;
+  // at least 116 KB so that one CTA (which owns all 512 TMEM columns) fits per SM
+  const size_t smem = std::max<size_t>(a_terms * a_bytes + (size_t)Cfg::G * 2 * b_bytes, 116 * 1024);
+  auto kern = step_tc_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int runs_per_cta = Cfg::G * Cfg::RG;
+  const int grid = (sc.n_runs + runs_per_cta - 1) / runs_per_cta;
+  kern<<<grid, 128 * Cfg::G, smem, st>>>((const uint8_t*)c->d_Jbf16, (float*)c->d_X, c->d_h,
+                                         c->d_seeds, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Canonical K-major, no-swizzle image of J for the A operand: 128 rows (M) x KP
+// (K) BF16, core matrices of 8 rows x 16 bytes; element (m, k) at byte
+// (m%8)*16 + (k%8)*2 + (m/8)*(KP/8)*128 + (k/8)*128.  Real J gets a second
+// image holding the BF16 residual J - bf16(J).
+cudaError_t prepare_tc_operand(chym_ctx* c) {
+  if (c->d_Jbf16) return cudaSuccess;
+  const int N = c->N, KP = (N + 15) / 16 * 16;
+  const int terms = c->kind == CHYM_J_PM1 ? 1 : 2;
+  const size_t img = 128u * (size_t)KP;  // elements per term
+  std::vector<uint16_t> h(terms * img, 0);
+  for (int m = 0; m < 128; ++m)
+    for (int k = 0; k < KP; ++k) {
+      const double v = (m < N && k < N) ? c->h_J[(size_t)m * N + k] : 0.0;
+      const uint16_t hi = bf16_bits((float)v);
+      const uint16_t lo = bf16_bits((float)(v - (double)bf16_value(hi)));
+      const size_t off = (size_t)(m % 8) * 8 + (k % 8) + (size_t)(m / 8) * (KP / 8) * 64 +
+                         (size_t)(k / 8) * 64;  // in elements
+      h[off] = hi;
+      if (terms > 1) h[img + off] = lo;
+    }
+  cudaError_t e = cudaMalloc(&c->d_Jbf16, h.size() * sizeof(uint16_t));
+  if (e != cudaSuccess) return e;
+  c->jbf16_ld = KP;
+  return cudaMemcpy(c->d_Jbf16, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
+  if (c->N > 128) return cudaErrorNotSupported;
+  cudaError_t e = prepare_tc_operand(c);
+  if (e != cudaSuccess) return e;
+  switch (c->D) {
+    case 1: return launch_tc_typed<1>(c, sc, st);
+    case 2: return launch_tc_typed<2>(c, sc, st);
+    case 3: return launch_tc_typed<3>(c, sc, st);
+    case 4: return launch_tc_typed<4>(c, sc, st);
+    case 5: return launch_tc_typed<5>(c, sc, st);
+    case 6: return launch_tc_typed<6>(c, sc, st);
+    case 7: return launch_tc_typed<7>(c, sc, st);
+    case 8: return launch_tc_typed<8>(c, sc, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace chym

@@ -239,3 +239,102 @@ def test_ground_state_references_match_checker():
         ctx.close()
     for N in (6, 10, 20, 100):
         assert chym.ground_state_mobius(N) == O.ground_state_mobius(N, -1.0, -1.0)
+
+
+# ---------------------------------------------------------------------------
+# tensor-core path: J on tcgen05 in BF16, x split into BF16 hi + lo, FP32 state
+# ---------------------------------------------------------------------------
+BF16_CASES = [
+    # N, D, n_h, reps, steps, graph
+    (100, 4, 4, 7, 60, "sk"),        # 28 runs: a ragged group
+    (100, 2, 2, 33, 60, "mobius"),   # 66 runs: two CTAs, second one nearly empty
+    (100, 3, 3, 11, 60, "sk"),
+    (20, 3, 8, 4, 80, "sk"),
+    (37, 8, 3, 5, 40, "sparse"),     # two Philox blocks per spin, 4-run chunks
+    (128, 5, 2, 9, 40, "sk"),        # full 128-lane tile, three groups per CTA
+    (64, 6, 2, 4, 40, "sk"),
+    (13, 7, 1, 5, 40, "sk"),
+    (1, 1, 1, 3, 20, "sk"),
+    (61, 1, 2, 70, 50, "sparse"),    # D = 1: the CIM
+    (90, 4, 2, 6, 40, "gauss"),      # real J: three-term split
+]
+
+
+@pytest.mark.parametrize("N,D,n_h,reps,steps,graph", BF16_CASES)
+def test_bf16x2_state_matches_checker(N, D, n_h, reps, steps, graph):
+    ctx, J, X, Xo = _run_both(N, D, n_h, reps, steps, chym.PREC_BF16X2, graph)
+    assert np.all(np.isfinite(X))
+    assert _rel_err(X, Xo) <= 1e-4
+    ctx.close()
+
+
+def test_bf16x2_energies_and_continuation():
+    N, D, n_h, reps, K = 100, 4, 4, 16, 400
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 21)
+    prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+    sch = chym.Schedule(1, K // 2, K)
+    a = chym.Context(J, D)
+    a.run(prm, h, seeds, K, sch)
+    Xa, _ = a.get_state()
+    E, S = a.energy(spins=True)
+    s = chym.unpack_spins(S, N)
+    assert np.array_equal(s, O.readout(Xa))
+    assert np.array_equal(E, O.ising_energies(J, s))
+    # continuing in two launches is bit-identical on the GPU
+    b = chym.Context(J, D)
+    b.run(prm, h, seeds, K // 4, sch)
+    b.run(prm, None, None, K - K // 4, sch, n_runs=len(seeds))
+    Xb, kb = b.get_state()
+    assert kb == K and np.array_equal(Xa, Xb)
+    # and the FP32 SIMT form agrees with the tensor-core form on this short horizon
+    c = chym.Context(J, D)
+    c.run(chym.Params(eps=eps, prec=chym.PREC_FP32), h, seeds, K, sch)
+    Xc, _ = c.get_state()
+    assert _rel_err(Xa, Xc) <= 1e-4
+    for x in (a, b, c):
+        x.close()
+
+
+def test_bf16x2_full_size_launch_sampled_runs():
+    """The benchmark's launch shape (N=100, D=4, 4096 runs = 32 h x 128 replicas):
+    sampled runs against the checker, run by run."""
+    N, D, n_h, reps, K = 100, 4, 32, 128, 150
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 0xC0FFEE + 1)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+    sch = chym.Schedule(1, 10000, 20000)
+    ctx.run(prm, h, seeds, K, sch)
+    X, _ = ctx.get_state()
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(n_h * reps, 24, replace=False))
+    pick[0], pick[-1] = 0, n_h * reps - 1
+    hr = inputs.h_per_run(h, reps)[pick]
+    Xo = O.run(J, D, hr, seeds[pick], oracle_params(prm), oracle_schedule(sch), K)
+    assert _rel_err(X[pick], Xo) <= 1e-4
+    ctx.close()
+
+
+def test_bf16x2_statistical_parity_long_horizon():
+    """Moebius ladder N=100, D=4, 8 pumps x 32 replicas, 20000 steps (annealed over the
+    second half): per-pump success probability and the mean energy above the exact
+    ground state agree with the FP64 checker within 95% intervals."""
+    N, D, n_h, reps, K = 100, 4, 8, 32, 20000
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 5, graph="mobius")
+    E_gs = O.ground_state_mobius(N, -1.0, -1.0)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+    sch = chym.Schedule(1, K // 2, K)
+    ctx.run(prm, h, seeds, K, sch)
+    E = ctx.energy()
+    Xo = O.run(J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm), oracle_schedule(sch), K)
+    Eo = O.ising_energies(J, O.readout(Xo))
+    assert E.min() >= E_gs and Eo.min() >= E_gs
+    P = (E.reshape(n_h, reps) == E_gs).mean(1)
+    Po = (Eo.reshape(n_h, reps) == E_gs).mean(1)
+    for p, q in zip(P, Po):
+        half = 1.96 * np.sqrt(max(p * (1 - p), q * (1 - q), 1.0 / reps) * 2.0 / reps)
+        assert abs(p - q) <= half + 1e-12
+    d, do = E - E_gs, Eo - E_gs
+    se = np.sqrt(d.var() / d.size + do.var() / do.size)
+    assert abs(d.mean() - do.mean()) <= 1.96 * se + 1e-9
+    ctx.close()
