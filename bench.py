@@ -225,7 +225,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chym", choices=["chym", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["bf16x2", "fp32"])
+    ap.add_argument("--prec", default="bf16x2", choices=["bf16x2", "fp32"])
+    ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sim-steps", type=int, default=STEPS, help=argparse.SUPPRESS)
@@ -279,27 +280,63 @@ def main():
             c1.close()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    ev = []
+    streams = [torch.cuda.Stream(dev) for _ in jobs]
+    spans = []
 
     def one_step(record=False):
-        """init + sim_steps steps + energy + stats for every (graph, D); device inputs.
+        """init + sim_steps steps + energy for every (graph, D), each on its own stream so
+        the six launches share the GPU; then the ground-state statistics.  Device inputs.
         Returns the ground-state hits of this step."""
         flush.fill_(1.0)
-        hits = 0
-        for j in jobs:
-            if record:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+        fork = torch.cuda.Event(enable_timing=record)
+        fork.record(stream)
+        marks = []
+        for j, s in zip(jobs, streams):
+            s.wait_event(fork)
+            e0 = torch.cuda.Event(enable_timing=record)
+            e1 = torch.cuda.Event(enable_timing=record)
+            e0.record(s)
             j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), N_H, j["d_seeds"].data_ptr(),
-                                N_H * REPS, sim_steps, j["sched"], sp)
-            if record:
-                e1.record(stream)
-                ev.append((j, e0, e1))
-            j["ctx"].energy_device(j["d_E"].data_ptr(), 0, sp)
-            if record:
-                hits += int(j["ctx"].stats(gs[j["name"]], 0, sp)["n_hits"])
+                                N_H * REPS, sim_steps, j["sched"], s.cuda_stream)
+            e1.record(s)
+            j["ctx"].energy_device(j["d_E"].data_ptr(), 0, s.cuda_stream)
+            marks.append((e0, e1))
+        for s in streams:
+            stream.wait_stream(s)
+        hits = 0
+        if record:
+            spans.append((fork, marks))
+            for j, s in zip(jobs, streams):
+                hits += int(j["ctx"].stats(gs[j["name"]], 0, s.cuda_stream)["n_hits"])
         return hits
+
+    def set_prec(pv):
+        for j in jobs:
+            j["prm"].prec = pv
+
+    def timed_region(K):
+        """Barrier, K bench steps bracketed by CUDA events, barrier; max over ranks."""
+        spans.clear()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        hits = 0
+        for _ in range(K):
+            hits += one_step(record=True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        el = t_start.elapsed_time(t_end) / 1e3
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+            ht = torch.tensor([hits], device=dev, dtype=torch.float64)
+            dist.all_reduce(ht)
+            hits = int(ht.item())
+        return el, hits
 
     # warm-up; the SK reference also takes the best energy the runs found (best known)
     for _ in range(args.warmup):
@@ -311,35 +348,22 @@ def main():
 
     # ---------------- timed region: device-resident inputs ----------------
     clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    hits_total = 0
-    for _ in range(args.steps):
-        hits_total += one_step(record=True)
-    t_end.record(stream)
-    torch.cuda.synchronize()
+    elapsed, hits_total = timed_region(args.steps)
     clock_info = clocks.stop()
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        ht = torch.tensor([hits_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(ht)
-        hits_total = int(ht.item())
-
     work_step = sum(N_SPINS * j["D"] * N_H * REPS * sim_steps for j in jobs)
     value = work_step * args.steps * world / elapsed
-    # roofline of the dominant kernel (the step kernel), from its launches' events
-    dur = sum(e0.elapsed_time(e1) / 1e3 for _, e0, e1 in ev)
+    # roofline of the dominant kernel (the step kernel): its launches run concurrently,
+    # so achieved = their algorithmic work / span from the first start to the last end
+    dur = 0.0
+    for fork, marks in spans:
+        starts = [fork.elapsed_time(e0) for e0, _ in marks]
+        ends = [fork.elapsed_time(e1) for _, e1 in marks]
+        dur += (max(ends) - min(starts)) / 1e3
     on_alu = prec == chym.PREC_FP32
-    alg = sum(alu_ops_per_element(j["D"], N_SPINS if j["name"] == "sk" else j["nnz"], on_alu) *
-              N_SPINS * j["D"] * N_H * REPS * sim_steps for j, _, _ in ev)
+    alg = args.steps * sum(
+        alu_ops_per_element(j["D"], N_SPINS if j["name"] == "sk" else j["nnz"], on_alu) *
+        N_SPINS * j["D"] * N_H * REPS * sim_steps for j in jobs)
     achieved = alg / dur
     sm_mhz = clock_info.get("sm_mhz") or 1440.0
     peak = 152 * 128 * sm_mhz * 1e6
@@ -347,6 +371,18 @@ def main():
                 "unit": "Tlane-op/s", "frac": achieved / peak, "traffic": None,
                 "kernel": "chym step kernel (" + args.prec + ")",
                 "peak_note": "152 SMs x 128 FP32 lanes x median SM clock during the region"}
+
+    # ---------------- the plain FP32 form on the same workload ----------------
+    plain = None
+    if args.compare_plain and prec != chym.PREC_FP32:
+        set_prec(chym.PREC_FP32)
+        one_step()
+        el_p, hits_p = timed_region(args.steps)
+        set_prec(prec)
+        work_p = sum(N_SPINS * j["D"] * N_H * REPS * sim_steps for j in jobs)
+        plain = {"value": work_p * args.steps * world / el_p, "unit": UNIT,
+                 "gs_hits_per_s": hits_p / el_p, "ms_per_step": 1e3 * el_p / args.steps,
+                 "dtype": "f32", "form": "SIMT FP32 coupling product, same workload"}
 
     # ---------------- e2e: host inputs through the public API ----------------
     e2e = None
@@ -360,12 +396,15 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1.0)
-            for j, ph, ps, eh in zip(jobs, pin_h, pin_s, E_host):
+            fork = torch.cuda.Event()
+            fork.record(stream)
+            for j, ph, ps, s in zip(jobs, pin_h, pin_s, streams):
+                s.wait_event(fork)
                 j["ctx"].run(j["prm"], ph.numpy(), ps.numpy().view(np.uint64), sim_steps,
-                             j["sched"], sp)
-                Eh = j["ctx"].energy(stream=sp)
-                eh.copy_(torch.from_numpy(Eh))
-                j["ctx"].stats(gs[j["name"]], 0, sp)
+                             j["sched"], s.cuda_stream)
+            for j, eh, s in zip(jobs, E_host, streams):
+                eh.copy_(torch.from_numpy(j["ctx"].energy(stream=s.cuda_stream)))
+                j["ctx"].stats(gs[j["name"]], 0, s.cuda_stream)
         torch.cuda.synchronize()
         el2 = time.perf_counter() - t0
         if world > 1:
@@ -390,6 +429,9 @@ def main():
                 "gs_hits_per_s": hits_total / elapsed,
                 "e_gs": {k: float(v) for k, v in gs.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+                "plain_fp32": plain,
+                "gs_hits_ratio_vs_plain": (hits_total / elapsed) / plain["gs_hits_per_s"]
+                if plain and plain["gs_hits_per_s"] > 0 else None,
                 "gpu_launches": 4 * len(jobs) * args.steps}
         print(json.dumps(line), flush=True)
     for j in jobs:
