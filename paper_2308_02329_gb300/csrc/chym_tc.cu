@@ -173,6 +173,54 @@ __device__ __forceinline__ void store_b(uint8_t* Bhi, uint8_t* Blo, uint32_t off
   }
 }
 
+// One Philox4x32 round with round key (k0, k1).
+__device__ __forceinline__ void philox_round(uint4& c, uint32_t k0, uint32_t k1) {
+  const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x, p1 = (uint64_t)kPhiloxM1 * c.z;
+  c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                 (uint32_t)p0);
+}
+
+// Philox4x32-10 with the ten round keys precomputed (two rounds per uint4):
+// the key schedule depends on the run only, so it is built once per launch.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint4* __restrict__ rk) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const uint4 kk = rk[i];
+    philox_round(c, kk.x, kk.y);
+    philox_round(c, kk.z, kk.w);
+  }
+  return c;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Box-Muller for two runs at once: words (wr, wa) of run A and of run B give
+// zc = (-r_A cos t_A, -r_B cos t_B), zs = (-r sin t) with u = (w + 1/2) 2^-32,
+// r = sqrt(-2 ln u_r) * scale, t = 2 pi u_a - pi (the negation restores the
+// angle 2 pi u_a).  neg2ln2s2 = -2 ln(2) scale^2 folds the radius scaling.
+__device__ __forceinline__ void box_muller_x2(uint32_t wrA, uint32_t waA, uint32_t wrB,
+                                              uint32_t waB, float neg2ln2s2, float2& zc,
+                                              float2& zs) {
+  const float2 two32 = make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f);
+  const float2 half32 = make_float2(1.1641532182693481e-10f, 1.1641532182693481e-10f);
+  const float2 ang_m = make_float2(1.4629180792671596e-09f, 1.4629180792671596e-09f);
+  const float2 ang_c = make_float2(-3.1415926528582302f, -3.1415926528582302f);
+  const float2 ur = __ffma2_rn(make_float2((float)wrA, (float)wrB), two32, half32);
+  const float2 th = __ffma2_rn(make_float2((float)waA, (float)waB), ang_m, ang_c);
+  const float2 r2 = __fmul2_rn(make_float2(__log2f(ur.x), __log2f(ur.y)),
+                               make_float2(neg2ln2s2, neg2ln2s2));
+  const float2 r = make_float2(-sqrt_approx(r2.x), -sqrt_approx(r2.y));
+  float sA, cA, sB, cB;
+  __sincosf(th.x, &sA, &cA);
+  __sincosf(th.y, &sB, &cB);
+  zc = __fmul2_rn(r, make_float2(cA, cB));
+  zs = __fmul2_rn(r, make_float2(sA, sB));
+}
+
 template <int D>
 __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restrict__ Aimg,
                                                          float* __restrict__ X,
@@ -186,8 +234,8 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restri
   __shared__ int s_abort;
   __shared__ __align__(8) uint64_t s_mbar[G];
   __shared__ __align__(8) uint64_t s_abar;
-  __shared__ float s_ar[G][RG];
-  __shared__ uint2 s_key[G][RG];
+  __shared__ __align__(8) float s_ar[G][RG];
+  __shared__ uint4 s_rk[G][RG][5];  // Philox round keys of each run
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = warp >> 2, wq = warp & 3;
@@ -218,14 +266,18 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restri
   if (p < RG) {
     const int run = run0 + p;
     float ar = 0.f;
-    uint2 key = make_uint2(0u, 0u);
+    uint32_t k0 = 0u, k1 = 0u;
     if (p < nr) {
       ar = (float)(1.0 + (double)a.dt * (hg[run / a.replicas] - 1.0));
       const uint64_t s = seeds[run];
-      key = make_uint2((uint32_t)s, (uint32_t)(s >> 32));
+      k0 = (uint32_t)s;
+      k1 = (uint32_t)(s >> 32);
     }
     s_ar[g][p] = ar;
-    s_key[g][p] = key;
+    for (int i = 0; i < 5; ++i) {  // Weyl key schedule: round r uses key + r * (W0, W1)
+      s_rk[g][p][i] = make_uint4(k0 + (2u * i) * kPhiloxW0, k1 + (2u * i) * kPhiloxW1,
+                                 k0 + (2u * i + 1u) * kPhiloxW0, k1 + (2u * i + 1u) * kPhiloxW1);
+    }
   }
   // zero the B operands (K padding rows must stay finite zeros)
   for (uint32_t o = (uint32_t)(tid & 127) * 16u; o < 2u * b_bytes; o += 128u * 16u)
@@ -281,6 +333,8 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restri
   const uint32_t a_base = smem_addr(smem);
   const uint32_t bhi_base = smem_addr(Bhi), blo_base = smem_addr(Blo);
   const int ksteps = KP / 16;
+  const float neg2ln2s2 = -1.3862943611198906f * a.noise_scale * a.noise_scale;
+  const float2 ngdt = make_float2(-a.gdt, -a.gdt), nkdt = make_float2(-a.kdt, -a.kdt);
   uint32_t phase = 0;
   bool timed_out = false;
   if (nr > 0) {
@@ -329,12 +383,16 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restri
       tc_fence_after();
       // per-step coupling scale dt eps alpha_mu(k)
       float e_mu[D];
+      float2 e_mu2[D];
       {
         float ramp = 1.f;
         if (a.sched_kind == 1 && k >= a.k_anneal)
           ramp = k >= a.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(k - a.k_anneal) * a.inv_ramp);
 #pragma unroll
-        for (int mu = 0; mu < D; ++mu) e_mu[mu] = a.edt * (mu == 0 ? 1.f : ramp);
+        for (int mu = 0; mu < D; ++mu) {
+          e_mu[mu] = a.edt * (mu == 0 ? 1.f : ramp);
+          e_mu2[mu] = make_float2(e_mu[mu], e_mu[mu]);
+        }
       }
       if (ok) {
         for (int r0 = 0; r0 < RG; r0 += CH) {
@@ -347,28 +405,34 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restri
           tmem_wait_ld();
           if (live) {
 #pragma unroll
-            for (int j = 0; j < CH; ++j) {
+            for (int j = 0; j < CH; j += 2) {  // two runs at once, FP32x2 arithmetic
               const int r = r0 + j;
-              const float ar = s_ar[g][r];
-              const uint2 key = s_key[g][r];
-              float n2 = 0.f;
-#pragma unroll
-              for (int mu = 0; mu < D; ++mu) n2 = fmaf(x[mu][j], x[mu][j], n2);
-              const float t = fmaf(-a.gdt, n2, ar);
-              float z[4 * ((D + 3) / 4)];
+              const float2 ar = *reinterpret_cast<const float2*>(&s_ar[g][r]);
+              float2 z[4 * ((D + 3) / 4)];
 #pragma unroll
               for (int blk = 0; blk < (D + 3) / 4; ++blk) {
-                const uint4 w = philox4x32_10(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)k),
-                                              key.x, key.y);
-                box_muller_f32(w.x, w.y, a.noise_scale, z[4 * blk], z[4 * blk + 1]);
-                if (D - 4 * blk > 2) box_muller_f32(w.z, w.w, a.noise_scale, z[4 * blk + 2], z[4 * blk + 3]);
-                else z[4 * blk + 2] = z[4 * blk + 3] = 0.f;
+                const uint4 c = noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)k);
+                const uint4 wA = philox_rk(c, s_rk[g][r]);
+                const uint4 wB = philox_rk(c, s_rk[g][r + 1]);
+                box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, z[4 * blk], z[4 * blk + 1]);
+                if (D - 4 * blk > 2)
+                  box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, z[4 * blk + 2], z[4 * blk + 3]);
               }
+              float2 xx[D], n2 = make_float2(0.f, 0.f);
 #pragma unroll
               for (int mu = 0; mu < D; ++mu) {
-                const float xm = x[mu][j];
-                const float s = fmaf(-a.kdt * xm, xm, t);
-                x[mu][j] = fmaf(xm, s, fmaf(e_mu[mu], y[mu][j], z[mu]));
+                xx[mu] = make_float2(x[mu][j], x[mu][j + 1]);
+                n2 = __ffma2_rn(xx[mu], xx[mu], n2);
+              }
+              const float2 t = __ffma2_rn(ngdt, n2, ar);
+#pragma unroll
+              for (int mu = 0; mu < D; ++mu) {
+                const float2 q = __fmul2_rn(nkdt, xx[mu]);
+                const float2 sfac = __ffma2_rn(q, xx[mu], t);
+                const float2 inner = __ffma2_rn(e_mu2[mu], make_float2(y[mu][j], y[mu][j + 1]), z[mu]);
+                const float2 xn = __ffma2_rn(xx[mu], sfac, inner);
+                x[mu][j] = xn.x;
+                x[mu][j + 1] = xn.y;
               }
             }
           }
