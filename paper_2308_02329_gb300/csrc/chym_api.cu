@@ -172,7 +172,8 @@ chym_status check_run_args(chym_ctx* c, const chym_params* prm, int n_h, int n_r
 
 cudaError_t launch_step(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st) {
   if (prec == CHYM_PREC_FP64 || prec == CHYM_PREC_FP32) return launch_step_simt(c, sc, prec, st);
-  if (prec == CHYM_PREC_BF16X2) return launch_step_tc(c, sc, st);
+  if (prec == CHYM_PREC_BF16X2)
+    return c->N <= 128 ? launch_step_tc(c, sc, st) : launch_step_k2(c, sc, st);
   return cudaErrorNotSupported;
 }
 
@@ -249,6 +250,8 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_spins);
   free_dev(c->d_status);
   free_dev(c->d_scratch);
+  free_dev(c->d_Ak2);
+  free_dev(c->d_k2_ws);
   delete[] c->h_J;
   delete c;
   return CHYM_OK;

@@ -142,6 +142,9 @@ struct chym_ctx {
   unsigned* d_status = nullptr;
   void* d_scratch = nullptr;  // stats scratch
   size_t scratch_bytes = 0;
+  void* d_Ak2 = nullptr;      // J as A-operand blocks of the large-N path (lazily built)
+  void* d_k2_ws = nullptr;    // large-N workspace: column-major master state, BF16 blocks
+  size_t k2_ws_bytes = 0;
 };
 
 namespace chym {
@@ -149,6 +152,7 @@ namespace chym {
 cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_std);
 cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st);
 cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
+cudaError_t launch_step_k2(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st);
 cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol, double bin_w,
                          int n_bins, void* d_out, cudaStream_t st);

@@ -338,3 +338,71 @@ def test_bf16x2_statistical_parity_long_horizon():
     se = np.sqrt(d.var() / d.size + do.var() / do.size)
     assert abs(d.mean() - do.mean()) <= 1.96 * se + 1e-9
     ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# large-N path (N > 128): per-step tcgen05 GEMM with the update in its epilogue
+# ---------------------------------------------------------------------------
+K2_CASES = [
+    # N, D, n_h, reps, steps, graph
+    (129, 4, 2, 5, 30, "sk"),       # one spin past a full tile: 2 M tiles, ragged K
+    (200, 3, 3, 7, 30, "sk"),
+    (256, 2, 2, 40, 25, "sparse"),  # 80 runs: two column tiles, second one partial
+    (300, 8, 1, 9, 20, "sk"),
+    (150, 4, 2, 4, 20, "gauss"),    # real J: three-term split
+    (170, 1, 2, 70, 30, "sk"),      # the CIM
+    (140, 5, 1, 20, 20, "sk"),
+    (190, 6, 1, 17, 20, "sk"),
+    (133, 7, 1, 17, 20, "sparse"),
+    (1000, 4, 2, 3, 15, "sk"),
+]
+
+
+@pytest.mark.parametrize("N,D,n_h,reps,steps,graph", K2_CASES)
+def test_large_n_state_matches_checker(N, D, n_h, reps, steps, graph):
+    ctx, J, X, Xo = _run_both(N, D, n_h, reps, steps, chym.PREC_BF16X2, graph)
+    assert np.all(np.isfinite(X))
+    assert _rel_err(X, Xo) <= 1e-4
+    ctx.close()
+
+
+def test_large_n_continuation_and_energies():
+    N, D, n_h, reps, K = 257, 4, 2, 6, 40
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 13)
+    prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+    sch = chym.Schedule(1, 20, K)
+    a = chym.Context(J, D)
+    a.run(prm, h, seeds, K, sch)
+    Xa, _ = a.get_state()
+    b = chym.Context(J, D)
+    b.run(prm, h, seeds, 17, sch)
+    b.run(prm, None, None, K - 17, sch, n_runs=len(seeds))
+    Xb, _ = b.get_state()
+    assert np.array_equal(Xa, Xb)
+    E, S = a.energy(spins=True)
+    s = chym.unpack_spins(S, N)
+    assert np.array_equal(s, O.readout(Xa))
+    assert np.array_equal(E, O.ising_energies(J, s))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("N,runs,steps", [(1000, 16384, 12), (800, 65536, 6)])
+def test_large_n_full_size_launch_sampled_runs(N, runs, steps):
+    """Launch shapes of the dense SK workloads (N=1000 with 16384 runs, N=800 with
+    65536 runs, D=4): sampled runs against the checker, run by run."""
+    D, n_h = 4, 32
+    reps = runs // n_h
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 0xC0FFEE + N)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+    sch = chym.Schedule(1, 25000, 50000)
+    ctx.run(prm, h, seeds, steps, sch)
+    X, _ = ctx.get_state()
+    rng = np.random.default_rng(1)
+    pick = np.sort(rng.choice(runs, 12, replace=False))
+    pick[0], pick[-1] = 0, runs - 1
+    hr = inputs.h_per_run(h, reps)[pick]
+    Xo = O.run(J, D, hr, seeds[pick], oracle_params(prm), oracle_schedule(sch), steps)
+    assert _rel_err(X[pick], Xo) <= 1e-4
+    ctx.close()
