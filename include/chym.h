@@ -190,6 +190,30 @@ CHYM_API chym_status chym_ground_state_mobius(int N, double j_ring, double j_run
 CHYM_API chym_status chym_ground_state_search(chym_ctx* ctx, int restarts, int sweeps, uint64_t seed,
                                               double* E_out, uint64_t* spins_out);
 
+/* ---- Statistics without device allocation ----
+ * No counterpart in the paper: this entry point exists for callers that cannot
+ * allocate device memory at the point where they need the statistics (a host
+ * framework whose memory manager owns the whole device pool, a real-time loop
+ * with a fixed budget, or code that must avoid the device-wide synchronisation
+ * that cudaMalloc/cudaFree can cause).  It computes the same figures as
+ * chym_stats from energies the caller already holds on the device, without a
+ * context, and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * d_E: n_runs energies in device memory (h-major runs, as chym_energy_device
+ * writes them); kind decides exact (CHYM_J_PM1) or relative-tolerance hits.
+ * out, hits_per_h (nullable, n_h int64) and hist (nullable, n_bins int64) are
+ * host memory, filled as by chym_stats.  The kernel's result block lives in a
+ * fixed device array of about 545 KB compiled into the library, held by every
+ * GPU that loads it until the process exits.  Limits: n_h <= 4096 and
+ * n_bins <= 65536; larger sizes return CHYM_EINVAL.  The first call on a device
+ * looks up that array's device address (once per device); make that first call
+ * before any stream capture.  All calls share the one array: two calls whose
+ * work overlaps on the GPU (different streams, or different host threads) race
+ * and may return each other's numbers; serialise them.  Synchronises the stream. */
+CHYM_API chym_status chym_stats_noalloc(const double* d_E, int n_runs, int n_h, chym_jkind kind,
+                                        double E_gs, chym_stats_t* out, int64_t* hits_per_h,
+                                        int64_t* hist, int n_bins, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENO
 EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", "chym_run",
            "chym_run_device", "chym_energy", "chym_energy_device", "chym_stats",
            "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
-           "chym_ground_state_mobius", "chym_ground_state_search"]
+           "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc"]
 
 
 class ChymError(RuntimeError):
@@ -107,6 +107,8 @@ def lib():
         L.chym_ground_state_exact.argtypes = [vp, ctypes.POINTER(dbl), vp]
         L.chym_ground_state_mobius.argtypes = [i32, dbl, dbl, ctypes.POINTER(dbl)]
         L.chym_ground_state_search.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp]
+        L.chym_stats_noalloc.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(CStats), vp, vp,
+                                         i32, vp]
         for name in EXPORTS:
             if name != "chym_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -235,6 +237,22 @@ def ground_state_mobius(N, j_ring=-1.0, j_rung=-1.0):
     e = ctypes.c_double()
     _check(lib().chym_ground_state_mobius(int(N), float(j_ring), float(j_rung), ctypes.byref(e)))
     return e.value
+
+
+def stats_noalloc(d_E, n_runs, n_h, kind, E_gs, n_bins=0, stream=0):
+    """Figures of merit from device energies d_E (a device address) without any device
+    allocation by the library (see chym_stats_noalloc in include/chym.h)."""
+    st = CStats()
+    hits = np.zeros(n_h, dtype=np.int64)
+    hist = np.zeros(n_bins, dtype=np.int64) if n_bins else None
+    _check(lib().chym_stats_noalloc(ctypes.c_void_p(d_E), int(n_runs), int(n_h), int(kind),
+                                    float(E_gs), ctypes.byref(st), _ptr(hits), _ptr(hist),
+                                    int(n_bins), ctypes.c_void_p(stream)))
+    out = {f: getattr(st, f) for f, _ in CStats._fields_}
+    out["hits"] = hits
+    if hist is not None:
+        out["hist"] = hist
+    return out
 
 
 def unpack_spins(words, N):

@@ -7,6 +7,9 @@
 // figures of merit (i)-(iii) that follow Fig. 3 of arXiv 2308.02329.
 #include <math.h>
 
+#include <algorithm>
+#include <mutex>
+
 #include "chym_internal.cuh"
 
 namespace chym {
@@ -197,4 +200,116 @@ cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol
   return cudaGetLastError();
 }
 
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free statistics.
+//
+// Some callers cannot allocate device memory when they need the statistics:
+// code running under a memory manager that owns the whole device pool, callers
+// that must not trigger the device-wide synchronisation cudaMalloc/cudaFree can
+// imply, or real-time loops with a fixed memory budget.  For them the statistics
+// kernel writes its result block into this file-scope device array instead of a
+// context buffer.  Every GPU that loads the library holds the array until exit.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocMaxH = 4096;      // pump values
+constexpr int kNoAllocMaxBins = 65536;  // histogram bins
+constexpr size_t kNoAllocBytes =
+    sizeof(StatsOut) + sizeof(long long) * ((size_t)kNoAllocMaxH + kNoAllocMaxBins);
+static __device__ __align__(256) unsigned char g_stats_noalloc_scratch[kNoAllocBytes];
+
+// Device address of the array on each device, looked up once per device with that
+// device current (host code must not pass the array's name to a kernel).
+constexpr int kMaxDevices = 64;
+void* g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+cudaError_t noalloc_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_stats_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
 }  // namespace chym
+
+extern "C" CHYM_API chym_status chym_stats_noalloc(const double* d_E, int n_runs, int n_h,
+                                                   chym_jkind kind, double E_gs,
+                                                   chym_stats_t* out, int64_t* hits_per_h,
+                                                   int64_t* hist, int n_bins,
+                                                   void* cuda_stream) {
+  using namespace chym;
+  if (!d_E || !out) return fail(CHYM_EINVAL, "NULL argument");
+  if (n_h < 1 || n_runs < 1 || n_runs % n_h)
+    return fail(CHYM_EINVAL, "n_runs must be a positive multiple of n_h");
+  if (n_h > kNoAllocMaxH)
+    return fail(CHYM_EINVAL, "chym_stats_noalloc: n_h exceeds the fixed limit of 4096");
+  if (n_bins < 0 || n_bins > kNoAllocMaxBins || (hist && n_bins < 1))
+    return fail(CHYM_EINVAL, "chym_stats_noalloc: n_bins must be in [1, 65536] with a histogram");
+  if (kind != CHYM_J_PM1 && kind != CHYM_J_REAL) return fail(CHYM_EINVAL, "unknown J kind");
+  if (!isfinite(E_gs)) return fail(CHYM_EINVAL, "E_gs must be finite");
+  if (!hist) n_bins = 0;
+  void* scratch = nullptr;
+  cudaError_t e = noalloc_scratch_address(&scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(stats scratch)");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool pm1 = kind == CHYM_J_PM1;
+  const double tol = pm1 ? 0.0 : 1e-9 * fabs(E_gs);
+  double bin_w = pm1 ? 4.0 : 1e-3 * fabs(E_gs);
+  if (!(bin_w > 0.0)) bin_w = 1.0;
+  // the kernel initialises every word it reports (hits, bins, totals), so the
+  // previous call's contents never leak into this one
+  stats_kernel<<<1, kStatsThreads, sizeof(unsigned long long) * (size_t)n_h, st>>>(
+      d_E, n_runs, n_runs / n_h, n_h, E_gs, tol, bin_w, n_bins, (StatsOut*)scratch);
+  CHYM_CUDA_TRY(cudaGetLastError());
+  StatsOut head;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(&head, scratch, sizeof(head), cudaMemcpyDeviceToHost, st));
+  const long long* d_hits = reinterpret_cast<const long long*>((const StatsOut*)scratch + 1);
+  long long hits_small[64];
+  long long* hits = hits_per_h ? reinterpret_cast<long long*>(hits_per_h) : nullptr;
+  const bool need_tmp = !hits;
+  // per-pump counts are needed for P_max and W; without a caller buffer they are
+  // read in slices of 64 into the stack
+  if (hits) CHYM_CUDA_TRY(cudaMemcpyAsync(hits, d_hits, sizeof(long long) * n_h, cudaMemcpyDeviceToHost, st));
+  if (hist && n_bins)
+    CHYM_CUDA_TRY(cudaMemcpyAsync(hist, d_hits + n_h, sizeof(long long) * n_bins,
+                                  cudaMemcpyDeviceToHost, st));
+  CHYM_CUDA_TRY(cudaStreamSynchronize(st));
+  const int reps = n_runs / n_h;
+  double pmax = 0.0, psum = 0.0;
+  int nz = 0;
+  for (int i0 = 0; i0 < n_h; i0 += 64) {
+    const int cnt = std::min(64, n_h - i0);
+    const long long* hv = need_tmp ? hits_small : hits + i0;
+    if (need_tmp) {
+      CHYM_CUDA_TRY(cudaMemcpy(hits_small, d_hits + i0, sizeof(long long) * cnt, cudaMemcpyDeviceToHost));
+    }
+    for (int i = 0; i < cnt; ++i) {
+      const double P = (double)hv[i] / reps;
+      pmax = std::max(pmax, P);
+      psum += P;
+      if (hv[i] > 0) ++nz;
+    }
+  }
+  out->P_max = pmax;
+  out->W_range = nz ? psum / nz : 0.0;
+  out->W_scan = psum / n_h;
+  out->dE_mean = head.n_finite ? head.sum_dE / (double)head.n_finite : NAN;
+  out->best_E = head.best_E;
+  out->best_run = head.best_run;
+  out->n_finite = head.n_finite;
+  out->n_hits = head.n_hits;
+  return CHYM_OK;
+}
+
