@@ -1,18 +1,23 @@
-"""Benchmark of the CHYM GB300 simulator on the N=100 workload.
+"""Benchmark of the CHYM GB300 simulator.
 
-Workload (one bench step): the Moebius ladder N=100 (ring bonds -1 plus
-antipodal rungs -1) and an SK +-1 N=100 instance, each at hyperspin dimension
-D in {2 (XY machine, no annealing), 3, 4} with 4096 runs = 32 pump values x
-128 replicas, 20000 Euler-Maruyama steps (dt = 0.01; D >= 3 anneal linearly
-over the second half), then Ising readout, energies and ground-state hit
-statistics.  Metric: hyperspin-steps/s (N * D * runs * steps per second) and
-ground-state hits per second.
+Default workload ("n100", one bench step): the Moebius ladder N=100 (ring bonds
+-1 plus antipodal rungs -1) and an SK +-1 N=100 instance, each at hyperspin
+dimension D in {2 (XY machine, no annealing), 3, 4} with 4096 runs = 32 pump
+values x 128 replicas, 20000 Euler-Maruyama steps (dt = 0.01; D >= 3 anneal
+linearly over the second half), then the Ising readout, energies and
+ground-state statistics.  Other workloads (--workload): "sk1000" (SK +-1 and
+Gaussian N=1000, D=4, 16384 runs, 50000 steps) and "sk800" (SK +-1 N=800, D=4,
+65536 runs, 50000 steps), which run on the large-N tensor-core path.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x2|fp32]
-  python bench.py --impl reference ...   # the FP64 CPU checker on host cores
+Metric: hyperspin-steps/s (N * D * runs * steps per second) and ground-state
+hits per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n100|sk1000|sk800]
+  python bench.py --impl reference ...   # the FP64 CPU checker on the host cores
 
 Multi-GPU (torchrun): every rank runs its own replica of the workload with its
-own seeds (runs are independent); value = all ranks' work / max rank time.
+own seeds (runs are independent, no collective on the data path); value = all
+ranks' work / max rank time.
 """
 import argparse
 import json
@@ -22,6 +27,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from dataclasses import dataclass, field
 
 import numpy as np
 
@@ -30,27 +36,49 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GS hits/s and hyperspin-steps/s (N·D·runs·steps), mixed+learned vs plain FP32"
 UNIT = "hyperspin-steps/s"
-N_SPINS = 100
-D_LIST = (2, 3, 4)
-N_H = 32
-REPS = 128
-STEPS = 20000
 EPS_HAT = 0.5
 INSTANCE_SEED = 0xC0FFEE
+PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
-def workload_config(prec_name):
-    return {"workload": "moebius N=100 + SK+-1 N=100, D in {2,3,4}, 4096 runs/graph "
-                        "(32 h x 128 replicas), 20000 steps dt=0.01",
-            "graphs": ["moebius_ladder_100", "sk_pm1_100"], "D": list(D_LIST),
-            "runs_per_graph": N_H * REPS, "n_h": N_H, "replicas": REPS, "steps": STEPS,
-            "precision": prec_name, "l2": "flushed between steps (256 MiB write)"}
+@dataclass
+class Workload:
+    key: str
+    title: str
+    graphs: list            # (name, kind, N)
+    D: tuple
+    n_h: int
+    reps: int
+    steps: int
+    compare_plain: bool = True
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def runs(self):
+        return self.n_h * self.reps
 
 
-def make_instances(rank):
+WORKLOADS = {
+    "n100": Workload("n100", "moebius N=100 + SK+-1 N=100, D in {2,3,4}, 4096 runs/graph "
+                     "(32 h x 128 replicas), 20000 steps dt=0.01",
+                     [("moebius", "moebius", 100), ("sk", "sk", 100)], (2, 3, 4), 32, 128, 20000),
+    "sk1000": Workload("sk1000", "SK+-1 and Gaussian N(0,1/N) N=1000, D=4, 16384 runs "
+                       "(32 h x 512 replicas), 50000 steps dt=0.01",
+                       [("sk", "sk", 1000), ("gauss", "gauss", 1000)], (4,), 32, 512, 50000,
+                       compare_plain=False),
+    "sk800": Workload("sk800", "SK+-1 N=800, D=4, 65536 runs (32 h x 2048 replicas), "
+                      "50000 steps dt=0.01",
+                      [("sk", "sk", 800)], (4,), 32, 2048, 50000, compare_plain=False),
+}
+
+
+def build_graph(kind, N, rank):
     from paper_2308_02329_gb300 import inputs
-    return [("moebius", inputs.mobius_ladder(N_SPINS)),
-            ("sk", inputs.sk_pm1(N_SPINS, INSTANCE_SEED + 1 + 1000 * rank))]
+    if kind == "moebius":
+        return inputs.mobius_ladder(N)
+    if kind == "sk":
+        return inputs.sk_pm1(N, INSTANCE_SEED + 1 + 1000 * rank)
+    return inputs.gaussian(N, INSTANCE_SEED + 2 + 1000 * rank)
 
 
 def mode_for(D):
@@ -59,6 +87,23 @@ def mode_for(D):
     if D == 2:
         return 1e-3, 0
     return 0.1, 1
+
+
+def workload_config(w, prec_name, sim_steps):
+    return {"workload": w.title, "key": w.key,
+            "graphs": [f"{n}_{N}" for n, _, N in w.graphs], "D": list(w.D),
+            "runs_per_graph": w.runs, "n_h": w.n_h, "replicas": w.reps, "steps": sim_steps,
+            "precision": prec_name, "l2": "flushed between steps (256 MiB write)"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except (OSError, ValueError):
+        return dict(PEAK_FALLBACK), "fallback"
 
 
 def alu_ops_per_element(D, nnz_row, coupling_on_alu):
@@ -132,84 +177,72 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline_sample(target_s=10.0, threads=None):
-    """Time the FP64 CPU checker on a bounded sample of the same workload (all host cores)."""
+def oracle_jobs(w):
+    """(J, D, oracle params, oracle schedule) of every (graph, D) of a workload."""
+    import oracle.oracle as O
+    jobs = []
+    for name, kind, N in w.graphs:
+        J = build_graph(kind, N, 0)
+        lam = float(np.linalg.eigvalsh(J)[-1])
+        for D in w.D:
+            kappa, skind = mode_for(D)
+            prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
+                           eps=EPS_HAT / lam)
+            jobs.append((J, D, prm, O.Schedule(skind, w.steps // 2, w.steps)))
+    return jobs
+
+
+def time_oracle(jobs, runs, steps, threads):
+    """Wall time of the FP64 checker: every job, `runs` runs x `steps` steps + energies."""
     import oracle.oracle as O
     from paper_2308_02329_gb300 import inputs
-    threads = threads or os.cpu_count()
-    J = inputs.sk_pm1(N_SPINS, INSTANCE_SEED + 1)
-    lam = float(np.linalg.eigvalsh(J)[-1])
-    D = 4
-    prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=0.1, eps=EPS_HAT / lam)
-    sched = O.Schedule(1, STEPS // 2, STEPS)
-    h = inputs.pump_grid(1.0 - EPS_HAT, N_H)
-
-    def timed(runs, steps):
+    t0 = time.perf_counter()
+    for J, D, prm, sch in jobs:
+        N = J.shape[0]
         seeds = inputs.run_seeds(INSTANCE_SEED, runs)
-        hr = np.resize(np.repeat(h, max(1, runs // N_H)), runs)
-        X = O.init_state(N_SPINS, D, seeds, prm.init_std)
-        t0 = time.perf_counter()
-        O.integrate(J, X, hr, seeds, prm, sched, 0, steps, threads=threads)
-        return time.perf_counter() - t0
-
-    runs = max(threads * 2, 16)
-    probe_steps = 20
-    dt_probe = timed(runs, probe_steps)
-    steps = int(max(probe_steps, min(STEPS, probe_steps * target_s / max(dt_probe, 1e-6))))
-    el = timed(runs, steps)
-    value = N_SPINS * D * runs * steps / el
-    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"SK+-1 N=100 D=4, {runs} runs x {steps} steps (annealed from step "
-                      f"{STEPS // 2}), FP64, OpenMP over runs; {el:.1f} s"}
+        h = np.resize(inputs.pump_grid(1.0 - EPS_HAT, 8), runs)
+        X = O.init_state(N, D, seeds, prm.init_std)
+        O.integrate(J, X, h, seeds, prm, sch, 0, steps, threads=threads)
+        O.ising_energies(J, O.readout(X))
+    return time.perf_counter() - t0
 
 
-def run_reference(args, rank, world):
+def cpu_baseline_sample(w, target_s=10.0):
+    """The FP64 checker on a bounded sample of the same workload, on all host cores."""
+    threads = os.cpu_count()
+    jobs = oracle_jobs(w)
+    runs = max(2 * threads, 16)
+    probe = 20
+    t = time_oracle(jobs, runs, probe, threads)
+    steps = int(max(probe, min(w.steps, probe * target_s / max(t, 1e-6))))
+    el = time_oracle(jobs, runs, steps, threads)
+    work = sum(J.shape[0] * D * runs * steps for J, D, _, _ in jobs)
+    return {"value": work / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"every (graph, D) of the workload, {runs} runs x {steps} of "
+                      f"{w.steps} steps each, FP64, OpenMP over runs; {el:.1f} s"}
+
+
+def run_reference(args, w, rank, world):
     """The FP64 CPU checker as it stands, timed on the host cores on this workload."""
     if rank != 0:
         return 0
-    import oracle.oracle as O
-    from paper_2308_02329_gb300 import inputs
     threads = os.cpu_count()
-    insts = make_instances(0)
-    prepared = []
-    for name, J in insts:
-        lam = float(np.linalg.eigvalsh(J)[-1])
-        for D in D_LIST:
-            kappa, kind = mode_for(D)
-            prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
-                           eps=EPS_HAT / lam)
-            prepared.append((J, D, prm, O.Schedule(kind, STEPS // 2, STEPS)))
-    h = inputs.pump_grid(1.0 - EPS_HAT, N_H)
+    jobs = oracle_jobs(w)
     runs = max(threads, 16)
-    seeds = inputs.run_seeds(INSTANCE_SEED, runs)
-    hr = np.resize(np.repeat(h, max(1, runs // N_H)), runs)
-    # size each step to about 6 s of wall time
-    t0 = time.perf_counter()
-    for J, D, prm, sch in prepared:
-        X = O.init_state(N_SPINS, D, seeds, prm.init_std)
-        O.integrate(J, X, hr, seeds, prm, sch, 0, 50, threads=threads)
-    per_50 = time.perf_counter() - t0
-    steps = int(max(50, min(STEPS, 50 * 6.0 / max(per_50, 1e-6))))
-    work = sum(N_SPINS * D * runs * steps for _, D, _, _ in prepared)
-
-    def one():
-        for J, D, prm, sch in prepared:
-            X = O.init_state(N_SPINS, D, seeds, prm.init_std)
-            O.integrate(J, X, hr, seeds, prm, sch, 0, steps, threads=threads)
-            O.ising_energies(J, O.readout(X))
+    per_step_target = 6.0
+    t = time_oracle(jobs, runs, 20, threads)
+    steps = int(max(20, min(w.steps, 20 * per_step_target / max(t, 1e-6))))
     for _ in range(args.warmup):
-        one()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        one()
-    el = time.perf_counter() - t0
+        time_oracle(jobs, runs, steps, threads)
+    el = sum(time_oracle(jobs, runs, steps, threads) for _ in range(args.steps))
+    work = sum(J.shape[0] * D * runs * steps for J, D, _, _ in jobs)
     value = work * args.steps / el
-    sample = (f"per step: 2 graphs x D in {{2,3,4}}, {runs} runs x {steps} steps each "
-              f"(of 4096 x 20000), FP64, OpenMP over runs")
+    sample = (f"per step: every (graph, D) of the workload, {runs} runs x {steps} of {w.steps} "
+              f"steps each, FP64, OpenMP over runs")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config("fp64 (CPU checker)"),
+            "data": "synthetic", "config": workload_config(w, "fp64 (CPU checker)", w.steps),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
@@ -222,23 +255,30 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chym", choices=["chym", "reference"])
+    ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16x2", choices=["bf16x2", "fp32"])
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--sim-steps", type=int, default=STEPS, help=argparse.SUPPRESS)
+    ap.add_argument("--sim-steps", type=int, default=0,
+                    help="integration steps per run (default: the workload's); for profiling")
+    ap.add_argument("--replicas", type=int, default=0,
+                    help="replicas per pump value (default: the workload's); for profiling")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
+    w = WORKLOADS[args.workload]
+    if args.replicas:
+        w.reps = args.replicas
+    sim_steps = args.sim_steps or w.steps
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        return run_reference(args, rank, world)
+        return run_reference(args, w, rank, world)
 
     import torch
     import torch.distributed as dist
@@ -249,43 +289,41 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    sp = stream.cuda_stream
     prec = chym.PREC_BF16X2 if args.prec == "bf16x2" else chym.PREC_FP32
-    sim_steps = args.sim_steps
 
-    # ---------------- setup (untimed): instances, references, device inputs -------------
-    jobs = []
-    for gi, (name, J) in enumerate(make_instances(rank)):
-        for D in D_LIST:
-            ctx = chym.Context(J, D, chym.J_PM1)
+    # ---------------- setup (untimed): instances, references, device inputs ----------
+    jobs, gs = [], {}
+    for gi, (name, kind, N) in enumerate(w.graphs):
+        J = build_graph(kind, N, rank)
+        jkind = chym.J_REAL if kind == "gauss" else chym.J_PM1
+        for D in w.D:
+            ctx = chym.Context(J, D, jkind)
             lam = ctx.lambda_max()
-            kappa, kind = mode_for(D)
+            kappa, skind = mode_for(D)
             prm = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
                               eps=EPS_HAT / lam, prec=prec)
-            sched = chym.Schedule(kind, sim_steps // 2 if kind else 0, sim_steps)
-            h = inputs.pump_grid(1.0 - EPS_HAT, N_H)
-            seeds = inputs.run_seeds(INSTANCE_SEED + 7919 * rank + 97 * gi + D, N_H * REPS)
-            d_h = torch.from_numpy(h).to(dev)
-            d_seeds = torch.from_numpy(seeds.view(np.int64)).to(dev)
-            d_E = torch.empty(N_H * REPS, dtype=torch.float64, device=dev)
-            jobs.append(dict(name=name, J=J, D=D, ctx=ctx, prm=prm, sched=sched, h=h, seeds=seeds,
-                             d_h=d_h, d_seeds=d_seeds, d_E=d_E, nnz=int((J != 0).sum(1).mean())))
-    gs = {}
-    for name, J in make_instances(rank):
-        if name == "moebius":
-            gs[name] = chym.ground_state_mobius(N_SPINS)
+            sched = chym.Schedule(skind, sim_steps // 2 if skind else 0, sim_steps)
+            h = inputs.pump_grid(1.0 - EPS_HAT, w.n_h)
+            seeds = inputs.run_seeds(INSTANCE_SEED + 7919 * rank + 97 * gi + D, w.runs)
+            jobs.append(dict(name=name, N=N, J=J, D=D, ctx=ctx, prm=prm, sched=sched, h=h,
+                             seeds=seeds, d_h=torch.from_numpy(h).to(dev),
+                             d_seeds=torch.from_numpy(seeds.view(np.int64)).to(dev),
+                             d_E=torch.empty(w.runs, dtype=torch.float64, device=dev),
+                             nnz=int((J != 0).sum(1).mean())))
+        if kind == "moebius":
+            gs[name] = chym.ground_state_mobius(N)
         else:
-            c1 = chym.Context(J, 1)
-            gs[name] = c1.ground_state_search(restarts=64, sweeps=2000, seed=11)[0]
+            c1 = chym.Context(J, 1, jkind)
+            restarts, sweeps = (64, 2000) if N <= 200 else (4, 400)
+            gs[name] = c1.ground_state_search(restarts=restarts, sweeps=sweeps, seed=11)[0]
             c1.close()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
     streams = [torch.cuda.Stream(dev) for _ in jobs]
     spans = []
 
     def one_step(record=False):
         """init + sim_steps steps + energy for every (graph, D), each on its own stream so
-        the six launches share the GPU; then the ground-state statistics.  Device inputs.
+        the launches share the GPU; then the ground-state statistics.  Device inputs.
         Returns the ground-state hits of this step."""
         flush.fill_(1.0)
         fork = torch.cuda.Event(enable_timing=record)
@@ -296,8 +334,8 @@ def main():
             e0 = torch.cuda.Event(enable_timing=record)
             e1 = torch.cuda.Event(enable_timing=record)
             e0.record(s)
-            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), N_H, j["d_seeds"].data_ptr(),
-                                N_H * REPS, sim_steps, j["sched"], s.cuda_stream)
+            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), w.n_h, j["d_seeds"].data_ptr(),
+                                w.runs, sim_steps, j["sched"], s.cuda_stream)
             e1.record(s)
             j["ctx"].energy_device(j["d_E"].data_ptr(), 0, s.cuda_stream)
             marks.append((e0, e1))
@@ -320,15 +358,15 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
         hits = 0
         for _ in range(K):
             hits += one_step(record=True)
-        t_end.record(stream)
+        t1.record(stream)
         torch.cuda.synchronize()
-        el = t_start.elapsed_time(t_end) / 1e3
+        el = t0.elapsed_time(t1) / 1e3
         if world > 1:
             t = torch.tensor([el], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -338,21 +376,22 @@ def main():
             hits = int(ht.item())
         return el, hits
 
-    # warm-up; the SK reference also takes the best energy the runs found (best known)
+    # warm-up; the references of non-exact instances also take the best energy found
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
     for j in jobs:
-        if j["name"] == "sk":
-            gs["sk"] = min(gs["sk"], float(j["d_E"].min().item()))
+        if j["name"] != "moebius":
+            gs[j["name"]] = min(gs[j["name"]], float(j["d_E"].min().item()))
 
     # ---------------- timed region: device-resident inputs ----------------
     clocks = ClockSampler(local)
     clocks.start()
     elapsed, hits_total = timed_region(args.steps)
     clock_info = clocks.stop()
-    work_step = sum(N_SPINS * j["D"] * N_H * REPS * sim_steps for j in jobs)
+    work_step = sum(j["N"] * j["D"] * w.runs * sim_steps for j in jobs)
     value = work_step * args.steps * world / elapsed
+
     # roofline of the dominant kernel (the step kernel): its launches run concurrently,
     # so achieved = their algorithmic work / span from the first start to the last end
     dur = 0.0
@@ -360,27 +399,39 @@ def main():
         starts = [fork.elapsed_time(e0) for e0, _ in marks]
         ends = [fork.elapsed_time(e1) for _, e1 in marks]
         dur += (max(ends) - min(starts)) / 1e3
-    on_alu = prec == chym.PREC_FP32
-    alg = args.steps * sum(
-        alu_ops_per_element(j["D"], N_SPINS if j["name"] == "sk" else j["nnz"], on_alu) *
-        N_SPINS * j["D"] * N_H * REPS * sim_steps for j in jobs)
-    achieved = alg / dur
-    sm_mhz = clock_info.get("sm_mhz") or 1440.0
-    peak = 152 * 128 * sm_mhz * 1e6
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "Tlane-op/s", "frac": achieved / peak, "traffic": None,
-                "kernel": "chym step kernel (" + args.prec + ")",
-                "peak_note": "152 SMs x 128 FP32 lanes x median SM clock during the region"}
+    peaks, peak_src = measured_peaks()
+    large = max(j["N"] for j in jobs) > 128 and prec == chym.PREC_BF16X2
+    if large:
+        alg = args.steps * sum(2.0 * j["N"] ** 2 * j["D"] * w.runs * sim_steps for j in jobs)
+        issued = args.steps * sum(
+            2.0 * (128 * -(-j["N"] // 128)) ** 2 * j["D"] * w.runs * sim_steps *
+            (2 if j["name"] != "gauss" else 3) for j in jobs)
+        peak = peaks["bf16_tflops_sustained"] * 1e12
+        roofline = {"bound": "tensor", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
+                    "unit": "TFLOP/s", "frac": alg / dur / peak, "traffic": None,
+                    "issued_tflops": issued / dur / 1e12,
+                    "kernel": "large-N tcgen05 step (BF16 hi+lo, FP32 accumulate)",
+                    "peak_note": f"dense BF16 sustained, {peak_src}"}
+    else:
+        on_alu = prec == chym.PREC_FP32
+        alg = args.steps * sum(
+            alu_ops_per_element(j["D"], j["N"] if j["name"] == "sk" else j["nnz"], on_alu) *
+            j["N"] * j["D"] * w.runs * sim_steps for j in jobs)
+        sm_mhz = clock_info.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_mhz * 1e6
+        roofline = {"bound": "alu", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
+                    "unit": "Tlane-op/s", "frac": alg / dur / peak, "traffic": None,
+                    "kernel": "chym step kernel (" + args.prec + ")",
+                    "peak_note": "152 SMs x 128 FP32 lanes x median SM clock during the region"}
 
     # ---------------- the plain FP32 form on the same workload ----------------
     plain = None
-    if args.compare_plain and prec != chym.PREC_FP32:
+    if args.compare_plain and w.compare_plain and prec != chym.PREC_FP32:
         set_prec(chym.PREC_FP32)
         one_step()
         el_p, hits_p = timed_region(args.steps)
         set_prec(prec)
-        work_p = sum(N_SPINS * j["D"] * N_H * REPS * sim_steps for j in jobs)
-        plain = {"value": work_p * args.steps * world / el_p, "unit": UNIT,
+        plain = {"value": work_step * args.steps * world / el_p, "unit": UNIT,
                  "gs_hits_per_s": hits_p / el_p, "ms_per_step": 1e3 * el_p / args.steps,
                  "dtype": "f32", "form": "SIMT FP32 coupling product, same workload"}
 
@@ -389,7 +440,7 @@ def main():
     if not args.no_e2e:
         pin_h = [torch.from_numpy(j["h"]).pin_memory() for j in jobs]
         pin_s = [torch.from_numpy(j["seeds"].view(np.int64)).pin_memory() for j in jobs]
-        E_host = [torch.empty(N_H * REPS, dtype=torch.float64).pin_memory() for _ in jobs]
+        E_host = [torch.empty(w.runs, dtype=torch.float64).pin_memory() for _ in jobs]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -411,28 +462,32 @@ def main():
             t = torch.tensor([el2], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el2 = float(t.item())
-        h2d = sum(N_H * 8 + N_H * REPS * 8 for _ in jobs)
-        d2h = sum(N_H * REPS * 8 + 64 + N_H * 8 for _ in jobs)
+        h2d = sum(w.n_h * 8 + w.runs * 8 for _ in jobs)
+        d2h = sum(w.runs * 8 + 64 + w.n_h * 8 for _ in jobs)
         e2e = {"value": work_step * args.steps * world / el2, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline_sample()
+            cpu = cpu_baseline_sample(w)
+        # launches of our kernels per bench step: init + step + energy + stats for the
+        # small-N path; the large-N path adds 3 layout kernels and one launch per step
+        per_job = [4 if (j["N"] <= 128 or prec != chym.PREC_BF16X2) else 6 + sim_steps
+                   for j in jobs]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16x2+f32" if prec == chym.PREC_BF16X2 else "f32",
-                "data": "synthetic", "config": workload_config(args.prec),
+                "data": "synthetic", "config": workload_config(w, args.prec, sim_steps),
                 "gs_hits_per_s": hits_total / elapsed,
                 "e_gs": {k: float(v) for k, v in gs.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
                 "plain_fp32": plain,
                 "gs_hits_ratio_vs_plain": (hits_total / elapsed) / plain["gs_hits_per_s"]
                 if plain and plain["gs_hits_per_s"] > 0 else None,
-                "gpu_launches": 4 * len(jobs) * args.steps}
+                "gpu_launches": args.steps * sum(per_job)}
         print(json.dumps(line), flush=True)
     for j in jobs:
         j["ctx"].close()
