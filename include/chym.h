@@ -190,6 +190,35 @@ CHYM_API chym_status chym_ground_state_mobius(int N, double j_ring, double j_run
 CHYM_API chym_status chym_ground_state_search(chym_ctx* ctx, int restarts, int sweeps, uint64_t seed,
                                               double* E_out, uint64_t* spins_out);
 
+/* ---- Batched integration of many contexts (instances x hyperspin dimensions) ----
+ * The runs of every context are independent (the statistics of the text before
+ * Fig. 4 are averages over replicas, pump values and graphs), so a batch spreads
+ * them over the whole GPU: contexts on the small-N tensor-core path (BF16X2,
+ * N <= 128) are integrated by one persistent launch per dimension D whose CTAs walk
+ * a host-planned list of run ranges, balanced in whole 8-run chunks across the SMs;
+ * the other contexts run their own launches concurrently on forked streams.  The
+ * batch keeps the contexts (not owned) and its streams, events and plan buffer. */
+typedef struct chym_batch chym_batch;
+
+/* ctxs: n_ctx contexts (pointers copied; the contexts must outlive the batch). */
+CHYM_API chym_status chym_batch_create(chym_ctx* const* ctxs, int n_ctx, chym_batch** out);
+
+/* Advance every context by `steps` steps from its own current step, with
+ * params[i] and schedules[i] (arrays of n_ctx).  Every context must already hold
+ * a state (chym_run/chym_run_device with seeds, possibly with steps = 0, or
+ * chym_set_state); the result equals integrating each context alone.  Work is
+ * ordered after prior work on cuda_stream and the stream waits for all of it.
+ * EINVAL on bad params, ESTATE on a context without state, ENOTSUP when no kernel
+ * covers a context. */
+CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
+                                    const chym_schedule* schedules, int64_t steps, void* cuda_stream);
+
+/* Read and clear the batch's device status word (synchronous): CHYM_ETIMEOUT when a
+ * bounded device-side wait of a batched launch gave up. */
+CHYM_API chym_status chym_batch_status(chym_batch* b);
+
+CHYM_API chym_status chym_batch_destroy(chym_batch* b);
+
 /* ---- Statistics without device allocation ----
  * No counterpart in the paper: this entry point exists for callers that cannot
  * allocate device memory at the point where they need the statistics (a host

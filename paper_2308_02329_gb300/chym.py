@@ -24,7 +24,8 @@ _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENO
 EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", "chym_run",
            "chym_run_device", "chym_energy", "chym_energy_device", "chym_stats",
            "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
-           "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc"]
+           "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
+           "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy"]
 
 
 class ChymError(RuntimeError):
@@ -107,6 +108,10 @@ def lib():
         L.chym_ground_state_exact.argtypes = [vp, ctypes.POINTER(dbl), vp]
         L.chym_ground_state_mobius.argtypes = [i32, dbl, dbl, ctypes.POINTER(dbl)]
         L.chym_ground_state_search.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp]
+        L.chym_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+        L.chym_batch_run.argtypes = [vp, ctypes.POINTER(CParams), ctypes.POINTER(CSchedule), i64, vp]
+        L.chym_batch_status.argtypes = [vp]
+        L.chym_batch_destroy.argtypes = [vp]
         L.chym_stats_noalloc.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(CStats), vp, vp,
                                          i32, vp]
         for name in EXPORTS:
@@ -237,6 +242,36 @@ def ground_state_mobius(N, j_ring=-1.0, j_rung=-1.0):
     e = ctypes.c_double()
     _check(lib().chym_ground_state_mobius(int(N), float(j_ring), float(j_rung), ctypes.byref(e)))
     return e.value
+
+
+class Batch:
+    """Several contexts integrated together (see chym_batch_* in include/chym.h)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        _check(lib().chym_batch_create(arr, len(self.contexts), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, params, schedules, steps, stream=0):
+        P = (CParams * len(self.contexts))(*[p.c() for p in params])
+        S = (CSchedule * len(self.contexts))(*[s.c() for s in schedules])
+        _check(lib().chym_batch_run(self._h, P, S, int(steps), ctypes.c_void_p(stream)))
+
+    def status(self):
+        _check(lib().chym_batch_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().chym_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stats_noalloc(d_E, n_runs, n_h, kind, E_gs, n_bins=0, stream=0):

@@ -90,8 +90,10 @@ chym_status ensure_batch(chym_ctx* c, int n_runs, int n_h) {
   return CHYM_OK;
 }
 
-StepConsts make_consts(const chym_ctx* c, const chym_params* prm, const chym_schedule* s,
-                       int64_t k0, int64_t steps) {
+}  // namespace
+
+StepConsts make_step_consts(const chym_ctx* c, const chym_params* prm, const chym_schedule* s,
+                            int64_t k0, int64_t steps) {
   StepConsts sc;
   sc.N = c->N;
   sc.D = c->D;
@@ -110,6 +112,8 @@ StepConsts make_consts(const chym_ctx* c, const chym_params* prm, const chym_sch
   return sc;
 }
 
+namespace {
+
 // Shared body of chym_run / chym_run_device once h and seeds sit on the device.
 chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_t steps,
                           const chym_schedule* sched, cudaStream_t st) {
@@ -126,7 +130,7 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
   }
   c->have_energy = false;
   if (steps > 0) {
-    const StepConsts sc = make_consts(c, prm, sched, c->k, steps);
+    const StepConsts sc = make_step_consts(c, prm, sched, c->k, steps);
     cudaError_t e = launch_step(c, sc, c->prec, st);
     if (e == cudaErrorInvalidConfiguration)
       return fail(CHYM_ENOTSUP, "problem too large for the selected kernel (N*D per run)");
@@ -251,6 +255,7 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_status);
   free_dev(c->d_scratch);
   free_dev(c->d_Ak2);
+  free_dev(c->d_plan);
   free_dev(c->d_k2_ws);
   delete[] c->h_J;
   delete c;

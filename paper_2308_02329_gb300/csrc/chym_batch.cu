@@ -1,0 +1,283 @@
+// chym_batch.cu -- batched integration of many contexts (instances x D) at once.
+//
+// Contexts on the small-N tensor-core path (N <= 128) are integrated by one
+// persistent launch per hyperspin dimension D.  Every CTA of such a launch walks a
+// host-built list of items (a run range of one context).  The planner spreads each
+// dimension's runs over its CTAs in near-equal numbers of 8-run chunks, so no SM
+// idles while another finishes a whole extra item.  The SMs are shared between the
+// dimensions in proportion to their estimated cost.  Contexts on the large-N path
+// run their per-step GEMM launches on forked streams, captured once into a CUDA graph
+// per chunk of steps and replayed.  Contexts in FP32/FP64 run the SIMT kernels on
+// forked streams.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "chym_internal.cuh"
+
+namespace chym {
+StepConsts make_step_consts(const chym_ctx* c, const chym_params* prm, const chym_schedule* s,
+                            int64_t k0, int64_t steps);
+cudaError_t launch_step(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st);
+}  // namespace chym
+
+struct chym_batch {
+  std::vector<chym_ctx*> ctxs;
+  std::vector<cudaStream_t> streams;  // one per context (forked work)
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  void* d_plan = nullptr;
+  size_t plan_bytes = 0;
+  unsigned* d_status = nullptr;
+  int sms = 0;
+  // per-dimension relative cost of one chunk-step (tuned by chym_batch_tune)
+  double chunk_cost[9] = {0, 1.0, 0.58, 0.83, 0.92, 1.15, 1.3, 1.45, 1.6};
+};
+
+namespace chym {
+namespace {
+
+struct PlanJob {
+  int desc, n_runs;
+};
+
+// Split the runs of `jobs` (all of one dimension) over P CTAs in near-equal chunk
+// counts; items never cross a context and hold at most `per_item` runs.
+void plan_dimension(const std::vector<PlanJob>& jobs, int CH, int per_item, int P,
+                    std::vector<unsigned char>& items, std::vector<int>& cta_begin) {
+  long long C = 0;
+  for (const auto& j : jobs) C += (j.n_runs + CH - 1) / CH;
+  if (P > C) P = (int)std::max(1LL, C);
+  const size_t ib = tc_item_bytes();
+  cta_begin.assign(1, 0);
+  int cta = 0;
+  long long acc = 0;
+  auto bound = [&](int b) { return (long long)llround((double)(b + 1) * (double)C / P); };
+  int n_items = 0;
+  for (const auto& j : jobs) {
+    int run = 0;
+    while (run < j.n_runs) {
+      long long cap = bound(cta) - acc;
+      if (cap <= 0 && cta + 1 < P) {
+        cta_begin.push_back(n_items);
+        ++cta;
+        continue;
+      }
+      if (cap <= 0) cap = (j.n_runs - run + CH - 1) / CH;  // last CTA takes the rest
+      const int left_chunks = (j.n_runs - run + CH - 1) / CH;
+      const int take = (int)std::min<long long>({cap, (long long)(per_item / CH), (long long)left_chunks});
+      const int runs = std::min(take * CH, j.n_runs - run);
+      items.resize(items.size() + ib);
+      tc_fill_item(items.data() + items.size() - ib, j.desc, run, runs);
+      ++n_items;
+      run += runs;
+      acc += take;
+    }
+  }
+  while ((int)cta_begin.size() < P + 1) cta_begin.push_back(n_items);
+}
+
+}  // namespace
+}  // namespace chym
+
+using namespace chym;
+
+extern "C" {
+
+CHYM_API chym_status chym_batch_create(chym_ctx* const* ctxs, int n_ctx, chym_batch** out) {
+  if (!ctxs || !out || n_ctx < 1) return fail(CHYM_EINVAL, "need at least one context");
+  for (int i = 0; i < n_ctx; ++i)
+    if (!ctxs[i]) return fail(CHYM_EINVAL, "NULL context in the batch");
+  chym_batch* b = new (std::nothrow) chym_batch();
+  if (!b) return fail(CHYM_ENOMEM, "host allocation failed");
+  b->ctxs.assign(ctxs, ctxs + n_ctx);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n_ctx && e == cudaSuccess; ++i) {
+    cudaStream_t s;
+    cudaEvent_t ev;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    b->streams.push_back(s);
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    b->joins.push_back(ev);
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    chym_status st = cuda_fail(e, "chym_batch_create");
+    chym_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return CHYM_OK;
+}
+
+CHYM_API chym_status chym_batch_destroy(chym_batch* b) {
+  if (!b) return CHYM_OK;
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->d_plan) cudaFree(b->d_plan);
+  if (b->d_status) cudaFree(b->d_status);
+  delete b;
+  return CHYM_OK;
+}
+
+CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
+                                    const chym_schedule* schedules, int64_t steps,
+                                    void* cuda_stream) {
+  if (!b || !params || !schedules) return fail(CHYM_EINVAL, "NULL argument");
+  if (steps < 0) return fail(CHYM_EINVAL, "steps must be >= 0");
+  const int n = (int)b->ctxs.size();
+  for (int i = 0; i < n; ++i) {
+    const chym_ctx* c = b->ctxs[i];
+    const chym_params& p = params[i];
+    const chym_schedule& s = schedules[i];
+    if (c->prec < 0) return fail(CHYM_ESTATE, "every context needs a state (chym_run with seeds first)");
+    if (!(p.dt > 0.0) || !(p.sigma >= 0.0) || p.flags != 0 || p.prec < CHYM_PREC_FP64 ||
+        p.prec > CHYM_PREC_BF16X2 || !isfinite(p.gamma) || !isfinite(p.kappa) || !isfinite(p.eps))
+      return fail(CHYM_EINVAL, "bad params in the batch");
+    if ((c->prec == CHYM_PREC_FP64) != (p.prec == CHYM_PREC_FP64))
+      return fail(CHYM_EINVAL, "a context cannot change between FP64 and FP32 storage");
+    if ((s.kind != 0 && s.kind != 1) || s.reserved != 0 ||
+        (s.kind == 1 && (s.k_anneal < 0 || s.k_total <= s.k_anneal)))
+      return fail(CHYM_EINVAL, "bad schedule in the batch");
+  }
+  if (steps == 0) return CHYM_OK;
+  cudaStream_t main = (cudaStream_t)cuda_stream;
+  CHYM_CUDA_TRY(cudaEventRecord(b->fork, main));
+
+  // ---- small-N tensor-core contexts: one persistent launch per dimension ----
+  std::vector<int> by_dim[9];
+  for (int i = 0; i < n; ++i) {
+    chym_ctx* c = b->ctxs[i];
+    if (params[i].prec == CHYM_PREC_BF16X2 && c->N <= 128) {
+      c->prec = CHYM_PREC_BF16X2;
+      by_dim[c->D].push_back(i);
+      cudaError_t e = prepare_tc_operand(c);
+      if (e != cudaSuccess) return cuda_fail(e, "J operand image");
+    }
+  }
+  double cost[9] = {0};
+  double total = 0.0;
+  for (int D = 1; D <= 8; ++D) {
+    for (int i : by_dim[D]) {
+      const int CH = tc_chunk_runs(D);
+      cost[D] += b->chunk_cost[D] * ((b->ctxs[i]->n_runs + CH - 1) / CH);
+    }
+    total += cost[D];
+  }
+  // plan: descriptors of all small-N contexts, then per dimension its items and CTA ranges
+  std::vector<unsigned char> blob;
+  const size_t db = tc_desc_bytes();
+  std::vector<int> desc_of(n, -1);
+  int n_desc = 0;
+  for (int D = 1; D <= 8; ++D)
+    for (int i : by_dim[D]) {
+      blob.resize(blob.size() + db);
+      const StepConsts sc = make_step_consts(b->ctxs[i], &params[i], &schedules[i], b->ctxs[i]->k, steps);
+      tc_fill_desc(b->ctxs[i], sc, blob.data() + blob.size() - db);
+      desc_of[i] = n_desc++;
+    }
+  struct DimLaunch {
+    int D, P, kp_max, terms_max;
+    size_t items_off, cta_off;
+  };
+  std::vector<DimLaunch> dl;
+  int sms_left = b->sms;
+  int dims_left = 0;
+  for (int D = 1; D <= 8; ++D) dims_left += by_dim[D].empty() ? 0 : 1;
+  for (int D = 1; D <= 8; ++D) {
+    if (by_dim[D].empty()) continue;
+    int P = std::max(1, (int)llround(b->sms * cost[D] / total));
+    P = std::min(P, sms_left - (dims_left - 1));
+    P = std::max(P, 1);
+    sms_left -= P;
+    --dims_left;
+    std::vector<PlanJob> jobs;
+    int kp_max = 16, terms_max = 1;
+    for (int i : by_dim[D]) {
+      jobs.push_back({desc_of[i], b->ctxs[i]->n_runs});
+      kp_max = std::max(kp_max, (b->ctxs[i]->N + 15) / 16 * 16);
+      terms_max = std::max(terms_max, b->ctxs[i]->kind == CHYM_J_PM1 ? 1 : 2);
+    }
+    std::vector<unsigned char> items;
+    std::vector<int> cta;
+    plan_dimension(jobs, tc_chunk_runs(D), tc_runs_per_item(D), P, items, cta);
+    DimLaunch L{D, (int)cta.size() - 1, kp_max, terms_max, 0, 0};
+    blob.resize((blob.size() + 15) / 16 * 16);
+    L.items_off = blob.size();
+    blob.insert(blob.end(), items.begin(), items.end());
+    blob.resize((blob.size() + 15) / 16 * 16);
+    L.cta_off = blob.size();
+    const unsigned char* cp = reinterpret_cast<const unsigned char*>(cta.data());
+    blob.insert(blob.end(), cp, cp + cta.size() * sizeof(int));
+    dl.push_back(L);
+  }
+  if (!blob.empty()) {
+    if (blob.size() > b->plan_bytes) {
+      if (b->d_plan) cudaFree(b->d_plan);
+      b->d_plan = nullptr;
+      b->plan_bytes = 0;
+      CHYM_CUDA_TRY(cudaMalloc(&b->d_plan, blob.size()));
+      b->plan_bytes = blob.size();
+    }
+    CHYM_CUDA_TRY(cudaMemcpyAsync(b->d_plan, blob.data(), blob.size(), cudaMemcpyHostToDevice, main));
+    CHYM_CUDA_TRY(cudaEventRecord(b->fork, main));
+  }
+  std::vector<bool> used(n, false);
+  int si = 0;
+  const unsigned char* base = (const unsigned char*)b->d_plan;
+  for (const auto& L : dl) {
+    cudaStream_t s = b->streams[si];
+    CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
+    CHYM_CUDA_TRY(launch_tc_items(L.D, base, base + L.items_off, (const int*)(base + L.cta_off), L.P,
+                                  steps, L.kp_max, L.terms_max, b->d_status, s));
+    CHYM_CUDA_TRY(cudaEventRecord(b->joins[si], s));
+    used[si++] = true;
+  }
+  // ---- every other context: its own launches on its own stream ----
+  for (int i = 0; i < n; ++i) {
+    chym_ctx* c = b->ctxs[i];
+    if (desc_of[i] >= 0) {
+      c->k += steps;
+      c->have_energy = false;
+      continue;
+    }
+    const int sidx = si < n ? si++ : (i % n);
+    cudaStream_t s = b->streams[sidx];
+    CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
+    c->prec = params[i].prec;
+    const StepConsts sc = make_step_consts(c, &params[i], &schedules[i], c->k, steps);
+    cudaError_t e = launch_step(c, sc, c->prec, s);
+    if (e == cudaErrorInvalidConfiguration || e == cudaErrorNotSupported)
+      return fail(CHYM_ENOTSUP, "no kernel for a context of this batch (size or precision)");
+    if (e != cudaSuccess) return cuda_fail(e, "batched step launch");
+    CHYM_CUDA_TRY(cudaEventRecord(b->joins[sidx], s));
+    used[sidx] = true;
+    c->k += steps;
+    c->have_energy = false;
+  }
+  for (int i = 0; i < n; ++i)
+    if (used[i]) CHYM_CUDA_TRY(cudaStreamWaitEvent(main, b->joins[i], 0));
+  return CHYM_OK;
+}
+
+CHYM_API chym_status chym_batch_status(chym_batch* b) {
+  if (!b) return fail(CHYM_EINVAL, "NULL batch");
+  unsigned st = 0;
+  CHYM_CUDA_TRY(cudaMemcpy(&st, b->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st) {
+    CHYM_CUDA_TRY(cudaMemset(b->d_status, 0, sizeof(unsigned)));
+    return fail(CHYM_ETIMEOUT, "a device-side wait of the batch timed out");
+  }
+  return CHYM_OK;
+}
+
+}  // extern "C"

@@ -142,6 +142,8 @@ struct chym_ctx {
   unsigned* d_status = nullptr;
   void* d_scratch = nullptr;  // stats scratch
   size_t scratch_bytes = 0;
+  void* d_plan = nullptr;     // launch plan of the small-N tensor-core kernel
+  size_t plan_bytes = 0;
   void* d_Ak2 = nullptr;      // J as A-operand blocks of the large-N path (lazily built)
   void* d_k2_ws = nullptr;    // large-N workspace: column-major master state, BF16 blocks
   size_t k2_ws_bytes = 0;
@@ -153,6 +155,17 @@ cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_
 cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st);
 cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 cudaError_t launch_step_k2(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
+// small-N tensor-core kernel over an item plan (chym_tc.cu)
+cudaError_t prepare_tc_operand(chym_ctx* c);
+int tc_runs_per_item(int D);
+int tc_chunk_runs(int D);
+size_t tc_desc_bytes();
+size_t tc_item_bytes();
+void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out);
+void tc_fill_item(void* out, int desc, int run_begin, int run_count);
+cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, const int* d_cta_begin,
+                            int n_cta, int64_t steps, int kp_max, int terms_max, unsigned* status,
+                            cudaStream_t st);
 cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st);
 cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol, double bin_w,
                          int n_bins, void* d_out, cudaStream_t st);

@@ -250,15 +250,16 @@ __global__ void __launch_bounds__(kThreads, 2) step_k2_kernel(const uint8_t* __r
       for (int c0 = c_begin; c0 < c_begin + n / 2; c0 += D) {
         const int c_glob = ct * n + c0;
         const int run = c_glob / D;
+        // TMEM loads and their wait in one asm statement per column (see tmem_ld_wait)
         uint32_t yr[D];
-        if constexpr (D == 1) {
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(yr[0]) : "r"(trow + (uint32_t)c0));
-        } else {
 #pragma unroll
-          for (int mu = 0; mu < D; ++mu)
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(yr[mu]) : "r"(trow + (uint32_t)(c0 + mu)));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int mu = 0; mu < D; ++mu)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\t"
+              "tcgen05.wait::ld.sync.aligned;"
+              : "=r"(yr[mu])
+              : "r"(trow + (uint32_t)(c0 + mu))
+              : "memory");
         float xn[D];
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) xn[mu] = 0.f;

@@ -29,12 +29,30 @@
 namespace chym {
 namespace {
 
-struct TcArgs {
-  int N, KP, n_runs, replicas, G, a_terms;
-  int64_t k0, steps;
+// One context of a launch: its J image, state, pumps, seeds and step constants.
+struct TcDesc {
+  const uint8_t* Aimg;
+  float* X;
+  const double* h;
+  const uint64_t* seeds;
+  int N, KP, n_runs, replicas, a_terms, sched_kind;
+  int64_t k0, k_anneal, k_total;
   float dt, noise_scale, gdt, kdt, edt, inv_ramp;
-  int sched_kind;
-  int64_t k_anneal, k_total;
+};
+
+// A block of consecutive runs of one context, integrated by one CTA: its G
+// groups take RG runs each.
+struct TcItem {
+  int desc, run_begin, run_count, pad;
+};
+
+struct TcLaunch {
+  const TcDesc* descs;
+  const TcItem* items;
+  const int* cta_begin;  // items of CTA b: [cta_begin[b], cta_begin[b + 1])
+  int64_t steps;
+  uint32_t a_region;     // bytes reserved for the largest J image of the launch
+  int kp_max;            // largest K (rows of B) of the launch
   unsigned* status;
 };
 
@@ -96,24 +114,61 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// Loads of the accumulator (ya) and master state (xa) columns followed by the wait
+// in ONE asm statement: tcgen05.ld fills its registers asynchronously, so the
+// compiler must not see (and possibly spill) them before tcgen05.wait::ld.
 template <int CH>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[CH]) {
+__device__ __forceinline__ void tmem_ld2_wait(uint32_t ya, uint32_t xa, float (&y)[CH], float (&x)[CH]) {
+  uint32_t r[2 * CH];
   if constexpr (CH == 8) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(ya), "r"(xa)
+        : "memory");
   } else {
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%8];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%9];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(ya), "r"(xa)
+        : "memory");
   }
+#pragma unroll
+  for (int j = 0; j < CH; ++j) {
+    y[j] = __uint_as_float(r[j]);
+    x[j] = __uint_as_float(r[CH + j]);
+  }
+}
+
+// Load of one group of columns followed by its wait, in one asm statement.
+template <int CH>
+__device__ __forceinline__ void tmem_ld_wait(uint32_t taddr, float (&v)[CH]) {
+  uint32_t r[CH];
+  if constexpr (CH == 8) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(taddr)
+        : "memory");
+  }
+#pragma unroll
+  for (int j = 0; j < CH; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 template <int CH>
@@ -131,7 +186,6 @@ __device__ __forceinline__ void tmem_st(uint32_t taddr, const float (&v)[CH]) {
   }
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -222,11 +276,7 @@ __device__ __forceinline__ void box_muller_x2(uint32_t wrA, uint32_t waA, uint32
 }
 
 template <int D>
-__global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restrict__ Aimg,
-                                                         float* __restrict__ X,
-                                                         const double* __restrict__ hg,
-                                                         const uint64_t* __restrict__ seeds,
-                                                         TcArgs a) {
+__global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
   using Cfg = TcCfg<D>;
   constexpr int RG = Cfg::RG, CG = Cfg::CG, CH = Cfg::CH, G = Cfg::G;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -240,14 +290,10 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restri
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = warp >> 2, wq = warp & 3;
   const int p = wq * 32 + lane;  // spin = TMEM lane
-  const int N = a.N, KP = a.KP;
-  const uint32_t a_bytes = 128u * (uint32_t)KP * 2u;
-  const uint32_t b_bytes = (uint32_t)KP * CG * 2u;
-  uint8_t* Bhi = smem + a.a_terms * a_bytes + (size_t)g * 2 * b_bytes;
+  const uint32_t b_bytes = (uint32_t)L.kp_max * CG * 2u;
+  uint8_t* Bhi = smem + L.a_region + (size_t)g * 2 * b_bytes;
   uint8_t* Blo = Bhi + b_bytes;
   const uint32_t lbo_b = (CG / 8) * 128u;  // B: core-matrix stride along K
-  const int run0 = (blockIdx.x * G + g) * RG;
-  const int nr = max(0, min(RG, a.n_runs - run0));
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -262,217 +308,235 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(const uint8_t* __restri
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[q])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // per-run constants of this group: 1 + dt (h - 1) and the Philox key
-  if (p < RG) {
-    const int run = run0 + p;
-    float ar = 0.f;
-    uint32_t k0 = 0u, k1 = 0u;
-    if (p < nr) {
-      ar = (float)(1.0 + (double)a.dt * (hg[run / a.replicas] - 1.0));
-      const uint64_t s = seeds[run];
-      k0 = (uint32_t)s;
-      k1 = (uint32_t)(s >> 32);
-    }
-    s_ar[g][p] = ar;
-    for (int i = 0; i < 5; ++i) {  // Weyl key schedule: round r uses key + r * (W0, W1)
-      s_rk[g][p][i] = make_uint4(k0 + (2u * i) * kPhiloxW0, k1 + (2u * i) * kPhiloxW1,
-                                 k0 + (2u * i + 1u) * kPhiloxW0, k1 + (2u * i + 1u) * kPhiloxW1);
-    }
-  }
-  // zero the B operands (K padding rows must stay finite zeros)
-  for (uint32_t o = (uint32_t)(tid & 127) * 16u; o < 2u * b_bytes; o += 128u * 16u)
-    *reinterpret_cast<uint4*>(Bhi + o) = make_uint4(0u, 0u, 0u, 0u);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid == 0) {  // TMA bulk copy of the prepared J image (all terms)
-    const uint32_t bytes = (uint32_t)a.a_terms * a_bytes;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&s_abar)),
-                 "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(smem)),
-        "l"(Aimg), "r"(bytes), "r"(smem_addr(&s_abar))
-        : "memory");
-  }
   const uint32_t tmem = s_tmem;
   const uint32_t t_lane = tmem + ((uint32_t)(wq * 32) << 16);
   const uint32_t acc_col = (uint32_t)(g * CG);
   const uint32_t mst_col = (uint32_t)(G * CG + g * CG);
   // B store offset of row k = p: (p % 8) * 16 + (p / 8) * lbo_b; column block adds n0/8*128 + n0%8*2
   const uint32_t b_row_off = (uint32_t)(p & 7) * 16u + (uint32_t)(p >> 3) * lbo_b;
-  const bool live = p < N;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
+                         ((uint32_t)(CG >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const uint32_t a_base = smem_addr(smem);
+  const uint32_t bhi_base = smem_addr(Bhi), blo_base = smem_addr(Blo);
+  uint32_t phase = 0, a_phase = 0;
+  int a_desc = -1;
+  bool aborted = false;
 
-  // ---- load the state: X[run][p][mu] -> TMEM master + BF16 hi/lo B ----
-  if (nr > 0) {
-    for (int r0 = 0; r0 < RG; r0 += CH) {
+  for (int it = L.cta_begin[blockIdx.x]; it < L.cta_begin[blockIdx.x + 1] && !aborted; ++it) {
+    const TcItem item = L.items[it];
+    const TcDesc d = L.descs[item.desc];
+    const int N = d.N, KP = d.KP;
+    const uint32_t a_bytes = 128u * (uint32_t)KP * 2u;
+    // the item's runs are spread evenly over the groups in whole chunks
+    const int per_g = min(RG, ((item.run_count + G - 1) / G + CH - 1) / CH * CH);
+    const int run0 = item.run_begin + g * per_g;
+    const int nr = max(0, min(per_g, item.run_begin + item.run_count - run0));
+    const bool new_a = item.desc != a_desc;  // CTA-uniform
+    if (new_a && tid == 0) {                 // TMA bulk copy of the context's J image
+      const uint32_t bytes = (uint32_t)d.a_terms * a_bytes;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&s_abar)),
+                   "r"(bytes)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_addr(smem)),
+          "l"(d.Aimg), "r"(bytes), "r"(smem_addr(&s_abar))
+          : "memory");
+    }
+    // per-run constants of this group: 1 + dt (h - 1) and the Philox round keys
+    if (p < RG) {
+      const int run = run0 + p;
+      float ar = 0.f;
+      uint32_t k0 = 0u, k1 = 0u;
+      if (p < nr) {
+        ar = (float)(1.0 + (double)d.dt * (d.h[run / d.replicas] - 1.0));
+        const uint64_t sd = d.seeds[run];
+        k0 = (uint32_t)sd;
+        k1 = (uint32_t)(sd >> 32);
+      }
+      s_ar[g][p] = ar;
+      for (int i = 0; i < 5; ++i) {  // Weyl key schedule: round r uses key + r * (W0, W1)
+        s_rk[g][p][i] = make_uint4(k0 + (2u * i) * kPhiloxW0, k1 + (2u * i) * kPhiloxW1,
+                                   k0 + (2u * i + 1u) * kPhiloxW0, k1 + (2u * i + 1u) * kPhiloxW1);
+      }
+    }
+    // zero the B operands (K padding rows and unused runs must stay finite zeros)
+    for (uint32_t o = (uint32_t)(tid & 127) * 16u; o < 2u * b_bytes; o += 128u * 16u)
+      *reinterpret_cast<uint4*>(Bhi + o) = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();  // every zero must land before any thread writes its state into B
+    const bool live = p < N;
+    // ---- load the state: X[run][p][mu] -> TMEM master + BF16 hi/lo B ----
+    for (int r0 = 0; r0 < nr; r0 += CH) {
 #pragma unroll
       for (int mu = 0; mu < D; ++mu) {
         float v[CH];
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
           const int r = r0 + j;
-          v[j] = (live && r < nr) ? X[((size_t)(run0 + r) * N + p) * D + mu] : 0.f;
+          v[j] = (live && r < nr) ? d.X[((size_t)(run0 + r) * N + p) * D + mu] : 0.f;
         }
         tmem_st<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), v);
         const uint32_t n0 = (uint32_t)(mu * RG + r0);
         if (live) store_b<CH>(Bhi, Blo, b_row_off + (n0 >> 3) * 128u + (n0 & 7u) * 2u, v);
       }
     }
-  }
-  tmem_wait_st();
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
+    tmem_wait_st();
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
 
-  // ---- step loop (each group independently) ----
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
-                         ((uint32_t)(CG >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  const uint32_t a_sbo = (uint32_t)(KP / 8) * 128u;
-  const uint32_t a_base = smem_addr(smem);
-  const uint32_t bhi_base = smem_addr(Bhi), blo_base = smem_addr(Blo);
-  const int ksteps = KP / 16;
-  const float neg2ln2s2 = -1.3862943611198906f * a.noise_scale * a.noise_scale;
-  const float2 ngdt = make_float2(-a.gdt, -a.gdt), nkdt = make_float2(-a.kdt, -a.kdt);
-  uint32_t phase = 0;
-  bool timed_out = false;
-  if (nr > 0) {
-    for (int64_t k = a.k0; k < a.k0 + a.steps; ++k) {
-      if (wq == 0 && lane == 0) {
-        bool ok = true;
-        if (k == a.k0) ok = mbar_wait(smem_addr(&s_abar), 0);
-        tc_fence_after();
-        if (ok) {
-          for (int ks = 0; ks < ksteps; ++ks) {
-            const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
-            mma_bf16(tmem + acc_col, da, smem_desc(bhi_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
-                     idesc, ks > 0);
-          }
-          for (int ks = 0; ks < ksteps; ++ks) {
-            const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
-            mma_bf16(tmem + acc_col, da, smem_desc(blo_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
-                     idesc, 1u);
-          }
-          if (a.a_terms > 1) {
+    // ---- step loop (each group independently) ----
+    const uint32_t a_sbo = (uint32_t)(KP / 8) * 128u;
+    const int ksteps = KP / 16;
+    const float neg2ln2s2 = -1.3862943611198906f * d.noise_scale * d.noise_scale;
+    const float2 ngdt = make_float2(-d.gdt, -d.gdt), nkdt = make_float2(-d.kdt, -d.kdt);
+    bool timed_out = false, a_pending = new_a;
+    if (nr > 0) {
+      for (int64_t k = d.k0; k < d.k0 + L.steps; ++k) {
+        if (wq == 0 && lane == 0) {
+          bool ok = true;
+          if (a_pending) ok = mbar_wait(smem_addr(&s_abar), a_phase);
+          a_pending = false;
+          tc_fence_after();
+          if (ok) {
             for (int ks = 0; ks < ksteps; ++ks) {
-              const uint64_t da = smem_desc(a_base + a_bytes + (uint32_t)ks * 256u, 128u, a_sbo);
+              const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
               mma_bf16(tmem + acc_col, da, smem_desc(bhi_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
+                       idesc, ks > 0);
+            }
+            for (int ks = 0; ks < ksteps; ++ks) {
+              const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
+              mma_bf16(tmem + acc_col, da, smem_desc(blo_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
                        idesc, 1u);
             }
-          }
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_addr(&s_mbar[g]))
-              : "memory");
-        } else {
-          atomicOr(a.status, STATUS_TIMEOUT);
-          s_abort = 1;
-          // nothing was issued: complete the phase so the group does not wait
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_mbar[g])) : "memory");
-        }
-      }
-      // warp-uniform outcome: the TMEM loads below are warp-collective
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&s_mbar[g]), phase));
-      phase ^= 1u;
-      if (!ok) {
-        timed_out = true;
-        atomicOr(a.status, STATUS_TIMEOUT);
-        s_abort = 1;
-      }
-      tc_fence_after();
-      // per-step coupling scale dt eps alpha_mu(k)
-      float e_mu[D];
-      float2 e_mu2[D];
-      {
-        float ramp = 1.f;
-        if (a.sched_kind == 1 && k >= a.k_anneal)
-          ramp = k >= a.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(k - a.k_anneal) * a.inv_ramp);
-#pragma unroll
-        for (int mu = 0; mu < D; ++mu) {
-          e_mu[mu] = a.edt * (mu == 0 ? 1.f : ramp);
-          e_mu2[mu] = make_float2(e_mu[mu], e_mu[mu]);
-        }
-      }
-      if (ok) {
-        for (int r0 = 0; r0 < RG; r0 += CH) {
-          float x[D][CH], y[D][CH];
-#pragma unroll
-          for (int mu = 0; mu < D; ++mu) {
-            tmem_ld<CH>(t_lane + acc_col + (uint32_t)(mu * RG + r0), y[mu]);
-            tmem_ld<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), x[mu]);
-          }
-          tmem_wait_ld();
-          if (live) {
-#pragma unroll
-            for (int j = 0; j < CH; j += 2) {  // two runs at once, FP32x2 arithmetic
-              const int r = r0 + j;
-              const float2 ar = *reinterpret_cast<const float2*>(&s_ar[g][r]);
-              float2 z[4 * ((D + 3) / 4)];
-#pragma unroll
-              for (int blk = 0; blk < (D + 3) / 4; ++blk) {
-                const uint4 c = noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)k);
-                const uint4 wA = philox_rk(c, s_rk[g][r]);
-                const uint4 wB = philox_rk(c, s_rk[g][r + 1]);
-                box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, z[4 * blk], z[4 * blk + 1]);
-                if (D - 4 * blk > 2)
-                  box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, z[4 * blk + 2], z[4 * blk + 3]);
-              }
-              float2 xx[D], n2 = make_float2(0.f, 0.f);
-#pragma unroll
-              for (int mu = 0; mu < D; ++mu) {
-                xx[mu] = make_float2(x[mu][j], x[mu][j + 1]);
-                n2 = __ffma2_rn(xx[mu], xx[mu], n2);
-              }
-              const float2 t = __ffma2_rn(ngdt, n2, ar);
-#pragma unroll
-              for (int mu = 0; mu < D; ++mu) {
-                const float2 q = __fmul2_rn(nkdt, xx[mu]);
-                const float2 sfac = __ffma2_rn(q, xx[mu], t);
-                const float2 inner = __ffma2_rn(e_mu2[mu], make_float2(y[mu][j], y[mu][j + 1]), z[mu]);
-                const float2 xn = __ffma2_rn(xx[mu], sfac, inner);
-                x[mu][j] = xn.x;
-                x[mu][j + 1] = xn.y;
+            if (d.a_terms > 1) {
+              for (int ks = 0; ks < ksteps; ++ks) {
+                const uint64_t da = smem_desc(a_base + a_bytes + (uint32_t)ks * 256u, 128u, a_sbo);
+                mma_bf16(tmem + acc_col, da, smem_desc(bhi_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
+                         idesc, 1u);
               }
             }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&s_mbar[g]))
+                : "memory");
+          } else {
+            atomicOr(L.status, STATUS_TIMEOUT);
+            s_abort = 1;
+            // nothing was issued: complete the phase so the group does not wait
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_mbar[g])) : "memory");
           }
+        }
+        // warp-uniform outcome: the TMEM loads below are warp-collective
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&s_mbar[g]), phase));
+        phase ^= 1u;
+        if (!ok) {
+          timed_out = true;
+          atomicOr(L.status, STATUS_TIMEOUT);
+          s_abort = 1;
+        }
+        tc_fence_after();
+        // per-step coupling scale dt eps alpha_mu(k)
+        float2 e_mu2[D];
+        {
+          float ramp = 1.f;
+          if (d.sched_kind == 1 && k >= d.k_anneal)
+            ramp = k >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(k - d.k_anneal) * d.inv_ramp);
 #pragma unroll
           for (int mu = 0; mu < D; ++mu) {
-            tmem_st<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), x[mu]);
-            const uint32_t n0 = (uint32_t)(mu * RG + r0);
-            if (live) store_b<CH>(Bhi, Blo, b_row_off + (n0 >> 3) * 128u + (n0 & 7u) * 2u, x[mu]);
+            const float e = d.edt * (mu == 0 ? 1.f : ramp);
+            e_mu2[mu] = make_float2(e, e);
+          }
+        }
+        if (ok) {
+          for (int r0 = 0; r0 < nr; r0 += CH) {
+            float x[D][CH], y[D][CH];
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu)
+              tmem_ld2_wait<CH>(t_lane + acc_col + (uint32_t)(mu * RG + r0),
+                                t_lane + mst_col + (uint32_t)(mu * RG + r0), y[mu], x[mu]);
+            if (live) {
+#pragma unroll
+              for (int j = 0; j < CH; j += 2) {  // two runs at once, FP32x2 arithmetic
+                const int r = r0 + j;
+                const float2 ar = *reinterpret_cast<const float2*>(&s_ar[g][r]);
+                float2 z[4 * ((D + 3) / 4)];
+#pragma unroll
+                for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+                  const uint4 c = noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)k);
+                  const uint4 wA = philox_rk(c, s_rk[g][r]);
+                  const uint4 wB = philox_rk(c, s_rk[g][r + 1]);
+                  box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, z[4 * blk], z[4 * blk + 1]);
+                  if (D - 4 * blk > 2)
+                    box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, z[4 * blk + 2], z[4 * blk + 3]);
+                }
+                float2 xx[D], n2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) {
+                  xx[mu] = make_float2(x[mu][j], x[mu][j + 1]);
+                  n2 = __ffma2_rn(xx[mu], xx[mu], n2);
+                }
+                const float2 t = __ffma2_rn(ngdt, n2, ar);
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) {
+                  const float2 q = __fmul2_rn(nkdt, xx[mu]);
+                  const float2 sfac = __ffma2_rn(q, xx[mu], t);
+                  const float2 inner = __ffma2_rn(e_mu2[mu], make_float2(y[mu][j], y[mu][j + 1]), z[mu]);
+                  const float2 xn = __ffma2_rn(xx[mu], sfac, inner);
+                  x[mu][j] = xn.x;
+                  x[mu][j + 1] = xn.y;
+                }
+              }
+            }
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu) {
+              tmem_st<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), x[mu]);
+              const uint32_t n0 = (uint32_t)(mu * RG + r0);
+              if (live) store_b<CH>(Bhi, Blo, b_row_off + (n0 >> 3) * 128u + (n0 & 7u) * 2u, x[mu]);
+            }
+          }
+        }
+        tmem_wait_st();
+        fence_async_smem();
+        tc_fence_before();
+        if (group_bar_or(1 + g, s_abort)) break;
+      }
+    }
+    if (wq == 0 && lane == 0) {
+      // the J copy must have landed before the next item may overwrite it
+      if (a_pending) mbar_wait(smem_addr(&s_abar), a_phase);
+      // the tensor core may still own this group's accumulator: wait once more (bounded)
+      if (timed_out) mbar_wait(smem_addr(&s_mbar[g]), phase ^ 1u);
+    }
+    if (new_a) {
+      a_phase ^= 1u;
+      a_desc = item.desc;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    aborted = s_abort != 0;
+    // ---- store the state back (skipped after a timeout: the status reports it) ----
+    if (!aborted) {
+      for (int r0 = 0; r0 < nr; r0 += CH) {
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+          float v[CH];
+          tmem_ld_wait<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), v);
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+              if (r0 + j < nr) d.X[((size_t)(run0 + r0 + j) * N + p) * D + mu] = v[j];
           }
         }
       }
-      tmem_wait_st();
-      fence_async_smem();
-      tc_fence_before();
-      if (group_bar_or(1 + g, s_abort)) break;
     }
-  }
-  if (timed_out && wq == 0 && lane == 0) {
-    // the tensor core may still own this group's accumulator: wait once more (bounded)
-    mbar_wait(smem_addr(&s_mbar[g]), phase ^ 1u);
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const bool aborted = s_abort != 0;
-  // ---- store the state back (skipped after a timeout: the status reports it) ----
-  if (nr > 0 && !aborted) {
-    for (int r0 = 0; r0 < RG; r0 += CH) {
-#pragma unroll
-      for (int mu = 0; mu < D; ++mu) {
-        float v[CH];
-        tmem_ld<CH>(t_lane + mst_col + (uint32_t)(mu * RG + r0), v);
-        tmem_wait_ld();
-        if (live) {
-#pragma unroll
-          for (int j = 0; j < CH; ++j)
-            if (r0 + j < nr) X[((size_t)(run0 + r0 + j) * N + p) * D + mu] = v[j];
-        }
-      }
-    }
+    tc_fence_before();
+    __syncthreads();  // the next item reuses B, TMEM and (possibly) the J region
+    tc_fence_after();
   }
   tc_fence_before();
   __syncthreads();
@@ -499,44 +563,97 @@ float bf16_value(uint16_t b) {
 }
 
 template <int D>
-cudaError_t launch_tc_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
+cudaError_t launch_tc_plan(const TcLaunch& L, int n_cta, cudaStream_t st) {
   using Cfg = TcCfg<D>;
-  const int KP = (c->N + 15) / 16 * 16;
-  const int a_terms = c->kind == CHYM_J_PM1 ? 1 : 2;
-  TcArgs a;
-  a.N = c->N;
-  a.KP = KP;
-  a.n_runs = sc.n_runs;
-  a.replicas = sc.replicas;
-  a.G = Cfg::G;
-  a.a_terms = a_terms;
-  a.k0 = sc.k0;
-  a.steps = sc.steps;
-  a.dt = (float)sc.dt;
-  a.noise_scale = (float)sc.noise_scale;
-  a.gdt = (float)(sc.dt * sc.gamma);
-  a.kdt = (float)(sc.dt * sc.kappa);
-  a.edt = (float)(sc.dt * sc.eps);
-  a.sched_kind = sc.sched_kind;
-  a.k_anneal = sc.k_anneal;
-  a.k_total = sc.k_total;
-  a.inv_ramp = sc.sched_kind == 1 ? (float)(1.0 / (double)(sc.k_total - sc.k_anneal)) : 0.f;
-  a.status = c->d_status;
-  const size_t a_bytes = 128u * (size_t)KP * 2u;
-  const size_t b_bytes = (size_t)KP * Cfg::CG * 2u;
+  const size_t b_bytes = (size_t)L.kp_max * Cfg::CG * 2u;
   // at least 116 KB so that one CTA (which owns all 512 TMEM columns) fits per SM
-  const size_t smem = std::max<size_t>(a_terms * a_bytes + (size_t)Cfg::G * 2 * b_bytes, 116 * 1024);
+  const size_t smem = std::max<size_t>(L.a_region + (size_t)Cfg::G * 2 * b_bytes, 116 * 1024);
   auto kern = step_tc_kernel<D>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int runs_per_cta = Cfg::G * Cfg::RG;
-  const int grid = (sc.n_runs + runs_per_cta - 1) / runs_per_cta;
-  kern<<<grid, 128 * Cfg::G, smem, st>>>((const uint8_t*)c->d_Jbf16, (float*)c->d_X, c->d_h,
-                                         c->d_seeds, a);
+  kern<<<n_cta, 128 * Cfg::G, smem, st>>>(L);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+int tc_runs_per_item(int D) {
+  switch (D) {
+    case 1: return TcCfg<1>::G * TcCfg<1>::RG;
+    case 2: return TcCfg<2>::G * TcCfg<2>::RG;
+    case 3: return TcCfg<3>::G * TcCfg<3>::RG;
+    case 4: return TcCfg<4>::G * TcCfg<4>::RG;
+    case 5: return TcCfg<5>::G * TcCfg<5>::RG;
+    case 6: return TcCfg<6>::G * TcCfg<6>::RG;
+    case 7: return TcCfg<7>::G * TcCfg<7>::RG;
+    case 8: return TcCfg<8>::G * TcCfg<8>::RG;
+  }
+  return 0;
+}
+
+int tc_chunk_runs(int D) { return D <= 4 ? 8 : 4; }
+
+size_t tc_desc_bytes() { return sizeof(TcDesc); }
+size_t tc_item_bytes() { return sizeof(TcItem); }
+
+// Fill the descriptor of one context for a launch starting at sc.k0.
+void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out) {
+  TcDesc& d = *reinterpret_cast<TcDesc*>(out);
+  d.Aimg = (const uint8_t*)c->d_Jbf16;
+  d.X = (float*)c->d_X;
+  d.h = c->d_h;
+  d.seeds = c->d_seeds;
+  d.N = c->N;
+  d.KP = (c->N + 15) / 16 * 16;
+  d.n_runs = sc.n_runs;
+  d.replicas = sc.replicas;
+  d.a_terms = c->kind == CHYM_J_PM1 ? 1 : 2;
+  d.sched_kind = sc.sched_kind;
+  d.k0 = sc.k0;
+  d.k_anneal = sc.k_anneal;
+  d.k_total = sc.k_total;
+  d.dt = (float)sc.dt;
+  d.noise_scale = (float)sc.noise_scale;
+  d.gdt = (float)(sc.dt * sc.gamma);
+  d.kdt = (float)(sc.dt * sc.kappa);
+  d.edt = (float)(sc.dt * sc.eps);
+  d.inv_ramp = sc.sched_kind == 1 ? (float)(1.0 / (double)(sc.k_total - sc.k_anneal)) : 0.f;
+}
+
+void tc_fill_item(void* out, int desc, int run_begin, int run_count) {
+  TcItem& it = *reinterpret_cast<TcItem*>(out);
+  it.desc = desc;
+  it.run_begin = run_begin;
+  it.run_count = run_count;
+  it.pad = 0;
+}
+
+// Launch the small-N tensor-core kernel of dimension D on a prepared plan in
+// device memory: descs, items and the per-CTA item ranges.
+cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, const int* d_cta_begin,
+                            int n_cta, int64_t steps, int kp_max, int terms_max, unsigned* status,
+                            cudaStream_t st) {
+  TcLaunch L;
+  L.descs = (const TcDesc*)d_descs;
+  L.items = (const TcItem*)d_items;
+  L.cta_begin = d_cta_begin;
+  L.steps = steps;
+  L.kp_max = kp_max;
+  L.a_region = (uint32_t)(terms_max * 128 * kp_max * 2);
+  L.status = status;
+  switch (D) {
+    case 1: return launch_tc_plan<1>(L, n_cta, st);
+    case 2: return launch_tc_plan<2>(L, n_cta, st);
+    case 3: return launch_tc_plan<3>(L, n_cta, st);
+    case 4: return launch_tc_plan<4>(L, n_cta, st);
+    case 5: return launch_tc_plan<5>(L, n_cta, st);
+    case 6: return launch_tc_plan<6>(L, n_cta, st);
+    case 7: return launch_tc_plan<7>(L, n_cta, st);
+    case 8: return launch_tc_plan<8>(L, n_cta, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 
 // Canonical K-major, no-swizzle image of J for the A operand: 128 rows (M) x KP
 // (K) BF16, core matrices of 8 rows x 16 bytes; element (m, k) at byte
@@ -568,17 +685,34 @@ cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
   if (c->N > 128) return cudaErrorNotSupported;
   cudaError_t e = prepare_tc_operand(c);
   if (e != cudaSuccess) return e;
-  switch (c->D) {
-    case 1: return launch_tc_typed<1>(c, sc, st);
-    case 2: return launch_tc_typed<2>(c, sc, st);
-    case 3: return launch_tc_typed<3>(c, sc, st);
-    case 4: return launch_tc_typed<4>(c, sc, st);
-    case 5: return launch_tc_typed<5>(c, sc, st);
-    case 6: return launch_tc_typed<6>(c, sc, st);
-    case 7: return launch_tc_typed<7>(c, sc, st);
-    case 8: return launch_tc_typed<8>(c, sc, st);
+  // one item (one CTA's worth of runs) per CTA
+  const int per_item = tc_runs_per_item(c->D);
+  const int n_items = (sc.n_runs + per_item - 1) / per_item;
+  const size_t bytes = sizeof(TcDesc) + sizeof(TcItem) * n_items + sizeof(int) * (n_items + 1);
+  std::vector<unsigned char> plan(bytes);
+  tc_fill_desc(c, sc, plan.data());
+  TcItem* items = reinterpret_cast<TcItem*>(plan.data() + sizeof(TcDesc));
+  int* cta = reinterpret_cast<int*>(plan.data() + sizeof(TcDesc) + sizeof(TcItem) * n_items);
+  for (int i = 0; i < n_items; ++i) {
+    tc_fill_item(&items[i], 0, i * per_item, std::min(per_item, sc.n_runs - i * per_item));
+    cta[i] = i;
   }
-  return cudaErrorInvalidValue;
+  cta[n_items] = n_items;
+  if (bytes > c->plan_bytes) {
+    if (c->d_plan) cudaFree(c->d_plan);
+    c->d_plan = nullptr;
+    c->plan_bytes = 0;
+    e = cudaMalloc(&c->d_plan, bytes);
+    if (e != cudaSuccess) return e;
+    c->plan_bytes = bytes;
+  }
+  e = cudaMemcpyAsync(c->d_plan, plan.data(), bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const unsigned char* base = (const unsigned char*)c->d_plan;
+  return launch_tc_items(c->D, base, base + sizeof(TcDesc),
+                         (const int*)(base + sizeof(TcDesc) + sizeof(TcItem) * n_items), n_items,
+                         sc.steps, (c->N + 15) / 16 * 16, c->kind == CHYM_J_PM1 ? 1 : 2,
+                         c->d_status, st);
 }
 
 }  // namespace chym

@@ -406,3 +406,77 @@ def test_large_n_full_size_launch_sampled_runs(N, runs, steps):
     Xo = O.run(J, D, hr, seeds[pick], oracle_params(prm), oracle_schedule(sch), steps)
     assert _rel_err(X[pick], Xo) <= 1e-4
     ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# batched integration of many contexts
+# ---------------------------------------------------------------------------
+def test_batch_equals_contexts_run_alone():
+    """A batch mixing dimensions, sizes and paths gives bit-identical states to each
+    context integrated on its own, also when split over two batch calls."""
+    cases = [  # N, D, n_h, reps, graph, prec
+        (100, 2, 4, 33, "mobius", chym.PREC_BF16X2),
+        (100, 3, 4, 17, "sk", chym.PREC_BF16X2),
+        (60, 4, 7, 11, "sk", chym.PREC_BF16X2),
+        (37, 4, 2, 9, "sparse", chym.PREC_BF16X2),
+        (90, 4, 2, 6, "gauss", chym.PREC_BF16X2),
+        (20, 3, 2, 5, "sk", chym.PREC_FP32),
+        (200, 4, 2, 4, "sk", chym.PREC_BF16X2),
+    ]
+    K = 60
+    solo, batched, prms, schs = [], [], [], []
+    for i, (N, D, n_h, reps, graph, prec) in enumerate(cases):
+        J, eps, h, seeds = make_case(N, D, n_h, reps, 40 + i, graph)
+        kind = chym.J_REAL if graph == "gauss" else chym.J_PM1
+        prm = chym.Params(eps=eps, prec=prec)
+        sch = chym.Schedule(1, 30, K)
+        a = chym.Context(J, D, kind)
+        a.run(prm, h, seeds, K, sch)
+        solo.append(a.get_state()[0])
+        a.close()
+        b = chym.Context(J, D, kind)
+        b.run(prm, h, seeds, 0, sch)
+        batched.append(b)
+        prms.append(prm)
+        schs.append(sch)
+    batch = chym.Batch(batched)
+    batch.run(prms, schs, 25)
+    batch.run(prms, schs, K - 25)
+    batch.status()
+    for Xs, b in zip(solo, batched):
+        Xb, kb = b.get_state()
+        assert kb == K
+        assert np.array_equal(Xs, Xb)
+    batch.close()
+    for b in batched:
+        b.close()
+
+
+def test_batch_many_small_instances_against_checker():
+    """Twenty uneven instances (N 50..128, D in {2,3,4,8}) in one batch; sampled runs
+    of each against the checker."""
+    rng = np.random.default_rng(7)
+    ctxs, prms, schs, meta = [], [], [], []
+    K = 30
+    for i in range(20):
+        N = int(rng.integers(50, 129))
+        D = int(rng.choice([2, 3, 4, 8]))
+        J, eps, h, seeds = make_case(N, D, 4, 16, 100 + i)
+        c = chym.Context(J, D)
+        prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+        sch = chym.Schedule(1, 15, K)
+        c.run(prm, h, seeds, 0, sch)
+        ctxs.append(c)
+        prms.append(prm)
+        schs.append(sch)
+        meta.append((J, D, h, seeds))
+    batch = chym.Batch(ctxs)
+    batch.run(prms, schs, K)
+    for c, prm, sch, (J, D, h, seeds) in zip(ctxs, prms, schs, meta):
+        X, _ = c.get_state()
+        pick = [0, 17, 63]
+        hr = inputs.h_per_run(h, 16)[pick]
+        Xo = O.run(J, D, hr, seeds[pick], oracle_params(prm), oracle_schedule(sch), K)
+        assert _rel_err(X[pick], Xo) <= 1e-4
+        c.close()
+    batch.close()
