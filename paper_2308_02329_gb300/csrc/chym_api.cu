@@ -256,6 +256,7 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_scratch);
   free_dev(c->d_Ak2);
   free_dev(c->d_plan);
+  k2_runner_release(c->k2_runner);
   free_dev(c->d_k2_ws);
   delete[] c->h_J;
   delete c;

@@ -32,6 +32,7 @@ struct chym_batch {
   size_t plan_bytes = 0;
   unsigned* d_status = nullptr;
   int sms = 0;
+  chym::K2Runner k2;
   // per-dimension relative cost of one chunk-step (tuned by chym_batch_tune)
   double chunk_cost[9] = {0, 1.0, 0.58, 0.83, 0.92, 1.15, 1.3, 1.45, 1.6};
 };
@@ -125,6 +126,7 @@ CHYM_API chym_status chym_batch_destroy(chym_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_plan) cudaFree(b->d_plan);
   if (b->d_status) cudaFree(b->d_status);
+  k2_runner_release(b->k2);
   delete b;
   return CHYM_OK;
 }
@@ -242,7 +244,41 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     CHYM_CUDA_TRY(cudaEventRecord(b->joins[si], s));
     used[si++] = true;
   }
-  // ---- every other context: its own launches on its own stream ----
+  // ---- large-N tensor-core contexts: grouped per-step launches, graph replay ----
+  {
+    std::vector<unsigned char> descs;
+    std::vector<int> dims, idx;
+    const size_t kb = k2_desc_bytes();
+    const int sidx = si < n ? si++ : 0;
+    cudaStream_t s = b->streams[sidx];
+    for (int i = 0; i < n; ++i) {
+      chym_ctx* c = b->ctxs[i];
+      if (desc_of[i] >= 0 || params[i].prec != CHYM_PREC_BF16X2) continue;
+      if (idx.empty()) CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
+      c->prec = CHYM_PREC_BF16X2;
+      descs.resize(descs.size() + kb);
+      const StepConsts sc = make_step_consts(c, &params[i], &schedules[i], c->k, steps);
+      cudaError_t e = k2_prepare(c, sc, s, descs.data() + descs.size() - kb);
+      if (e != cudaSuccess) return cuda_fail(e, "large-N preparation");
+      dims.push_back(c->D);
+      idx.push_back(i);
+    }
+    if (!idx.empty()) {
+      cudaError_t e = k2_integrate(b->k2, descs, dims, steps, b->d_status, s);
+      if (e != cudaSuccess) return cuda_fail(e, "large-N batched integration");
+      for (size_t t = 0; t < idx.size(); ++t) {
+        chym_ctx* c = b->ctxs[idx[t]];
+        e = k2_finish(c, descs.data() + t * kb, s);
+        if (e != cudaSuccess) return cuda_fail(e, "large-N state unpack");
+        c->k += steps;
+        c->have_energy = false;
+        desc_of[idx[t]] = -2;  // handled
+      }
+      CHYM_CUDA_TRY(cudaEventRecord(b->joins[sidx], s));
+      used[sidx] = true;
+    }
+  }
+  // ---- every other context (FP32/FP64): its own launches on its own stream ----
   for (int i = 0; i < n; ++i) {
     chym_ctx* c = b->ctxs[i];
     if (desc_of[i] >= 0) {
@@ -250,6 +286,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
       c->have_energy = false;
       continue;
     }
+    if (desc_of[i] == -2) continue;
     const int sidx = si < n ? si++ : (i % n);
     cudaStream_t s = b->streams[sidx];
     CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));

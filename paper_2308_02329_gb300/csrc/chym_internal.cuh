@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/chym.h"
 
@@ -116,6 +117,20 @@ __host__ __device__ __forceinline__ double alpha_of(int kind, int64_t k, int64_t
 
 }  // namespace chym
 
+namespace chym {
+// Launch state of the large-N path: device tables, a private capture stream and the
+// CUDA graph of a chunk of steps (re-captured when the tile table changes shape).
+struct K2Runner {
+  void* d_buf = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  size_t sig_tiles = 0;
+  std::vector<int> sig_dims;
+  void* sig_buf = nullptr;
+};
+}  // namespace chym
+
 // ------------------------------------------------------------------ context ---
 struct chym_ctx {
   int N = 0, D = 0;
@@ -147,6 +162,7 @@ struct chym_ctx {
   void* d_Ak2 = nullptr;      // J as A-operand blocks of the large-N path (lazily built)
   void* d_k2_ws = nullptr;    // large-N workspace: column-major master state, BF16 blocks
   size_t k2_ws_bytes = 0;
+  chym::K2Runner k2_runner;
 };
 
 namespace chym {
@@ -155,6 +171,14 @@ cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_
 cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st);
 cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 cudaError_t launch_step_k2(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
+// large-N path over several contexts (chym_k2.cu)
+cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void* desc_out);
+size_t k2_desc_bytes();
+cudaError_t k2_finish(chym_ctx* c, const void* desc, cudaStream_t st);
+cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
+                         const std::vector<int>& dims, int64_t steps, unsigned* status,
+                         cudaStream_t st);
+void k2_runner_release(K2Runner& R);
 // small-N tensor-core kernel over an item plan (chym_tc.cu)
 cudaError_t prepare_tc_operand(chym_ctx* c);
 int tc_runs_per_item(int D);
