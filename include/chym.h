@@ -167,6 +167,21 @@ CHYM_API chym_status chym_set_state(chym_ctx* ctx, const double* X, int n_runs, 
                            int n_h, const uint64_t* seeds, int64_t k, int32_t prec,
                            void* cuda_stream);
 
+/* Retire-and-reseed: the n runs listed in d_runs (device int32) restart from the
+ * new seeds d_new_seeds (device, n keys) at their local step 0 while the other
+ * runs continue: x(0) = init_std * N(0,1) from the new key (tag 1), and from then
+ * on the run's noise counter and annealing schedule use its local step
+ * k - k_reseed (k_reseed = the context's current step).  A reseeded run therefore
+ * follows exactly the trajectory of a fresh run with that seed.  Asynchronous;
+ * listed runs must be distinct and < n_runs. */
+CHYM_API chym_status chym_reseed_device(chym_ctx* ctx, const int32_t* d_runs, int n,
+                                        const uint64_t* d_new_seeds, double init_std,
+                                        void* cuda_stream);
+
+/* Per-run (re)seeding steps (device int64, n_runs): the local step of run r at the
+ * context's step k is k - offsets[r].  Asynchronous. */
+CHYM_API chym_status chym_get_offsets_device(chym_ctx* ctx, int64_t* d_offsets_out, void* cuda_stream);
+
 /* Shape of the current batch: n_runs, n_h and the current step (any may be NULL). */
 CHYM_API chym_status chym_info(chym_ctx* ctx, int* n_runs, int* n_h, int64_t* k);
 

@@ -25,7 +25,8 @@ EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", 
            "chym_run_device", "chym_energy", "chym_energy_device", "chym_stats",
            "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
            "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
-           "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy"]
+           "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
+           "chym_reseed_device", "chym_get_offsets_device"]
 
 
 class ChymError(RuntimeError):
@@ -108,6 +109,8 @@ def lib():
         L.chym_ground_state_exact.argtypes = [vp, ctypes.POINTER(dbl), vp]
         L.chym_ground_state_mobius.argtypes = [i32, dbl, dbl, ctypes.POINTER(dbl)]
         L.chym_ground_state_search.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp]
+        L.chym_reseed_device.argtypes = [vp, vp, i32, vp, dbl, vp]
+        L.chym_get_offsets_device.argtypes = [vp, vp, vp]
         L.chym_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
         L.chym_batch_run.argtypes = [vp, ctypes.POINTER(CParams), ctypes.POINTER(CSchedule), i64, vp]
         L.chym_batch_status.argtypes = [vp]
@@ -221,6 +224,15 @@ class Context:
         _check(lib().chym_ground_state_search(self._h, int(restarts), int(sweeps), int(seed),
                                               ctypes.byref(e), _ptr(S)))
         return e.value, unpack_spins(S, self.N)[0]
+
+    def reseed_device(self, d_runs, n, d_new_seeds, init_std, stream=0):
+        """Restart the n runs listed at device address d_runs (int32) from new seeds."""
+        _check(lib().chym_reseed_device(self._h, ctypes.c_void_p(d_runs), int(n),
+                                        ctypes.c_void_p(d_new_seeds), float(init_std),
+                                        ctypes.c_void_p(stream)))
+
+    def offsets_device(self, d_out, stream=0):
+        _check(lib().chym_get_offsets_device(self._h, ctypes.c_void_p(d_out), ctypes.c_void_p(stream)))
 
     def get_state(self, stream=0):
         n_runs, _, _ = self.info()

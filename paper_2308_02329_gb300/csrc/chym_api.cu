@@ -69,6 +69,7 @@ chym_status ensure_batch(chym_ctx* c, int n_runs, int n_h) {
   if (n_runs > c->cap_runs) {
     free_dev(c->d_X);
     free_dev(c->d_seeds);
+    free_dev(c->d_koff);
     free_dev(c->d_E);
     free_dev(c->d_spins);
     c->cap_runs = 0;
@@ -76,6 +77,7 @@ chym_status ensure_batch(chym_ctx* c, int n_runs, int n_h) {
     const int words = (c->N + 63) / 64;
     CHYM_CUDA_TRY(cudaMalloc(&c->d_X, xb));
     CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_seeds, sizeof(uint64_t) * n_runs));
+    CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_koff, sizeof(int64_t) * n_runs));
     CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_E, sizeof(double) * n_runs));
     CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_spins, sizeof(uint64_t) * (size_t)n_runs * words));
     c->x_bytes = xb;
@@ -109,6 +111,7 @@ StepConsts make_step_consts(const chym_ctx* c, const chym_params* prm, const chy
   sc.sched_kind = s->kind;
   sc.k_anneal = s->k_anneal;
   sc.k_total = s->k_total;
+  sc.koff = c->d_koff;
   return sc;
 }
 
@@ -120,6 +123,7 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
   if (init) {
     c->prec = prm->prec;
     c->k = 0;
+    CHYM_CUDA_TRY(cudaMemsetAsync(c->d_koff, 0, sizeof(int64_t) * c->n_runs, st));
     CHYM_CUDA_TRY(launch_init(c, c->prec, st, prm->init_std));
   } else if (prm->prec != c->prec) {
     // FP32 and BF16X2 share FP32 storage; FP64 storage cannot be continued in
@@ -250,6 +254,7 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_X);
   free_dev(c->d_h);
   free_dev(c->d_seeds);
+  free_dev(c->d_koff);
   free_dev(c->d_E);
   free_dev(c->d_spins);
   free_dev(c->d_status);
@@ -266,6 +271,26 @@ chym_status chym_destroy(chym_ctx* c) {
 chym_status chym_lambda_max(chym_ctx* c, double* out) {
   if (!c || !out) return fail(CHYM_EINVAL, "NULL argument");
   *out = host_lambda_max(c->h_J, c->N);
+  return CHYM_OK;
+}
+
+chym_status chym_reseed_device(chym_ctx* c, const int32_t* d_runs, int n, const uint64_t* d_new_seeds,
+                               double init_std, void* stream) {
+  if (!c) return fail(CHYM_EINVAL, "ctx is NULL");
+  if (c->prec < 0) return fail(CHYM_ESTATE, "no state: call chym_run first");
+  if (n < 0 || (n > 0 && (!d_runs || !d_new_seeds))) return fail(CHYM_EINVAL, "bad run list");
+  if (!(init_std >= 0.0) || !isfinite(init_std)) return fail(CHYM_EINVAL, "init_std must be >= 0");
+  if (n == 0) return CHYM_OK;
+  CHYM_CUDA_TRY(launch_reseed(c, d_runs, n, d_new_seeds, init_std, (cudaStream_t)stream));
+  c->have_energy = false;
+  return CHYM_OK;
+}
+
+chym_status chym_get_offsets_device(chym_ctx* c, int64_t* d_koff_out, void* stream) {
+  if (!c || !d_koff_out) return fail(CHYM_EINVAL, "NULL argument");
+  if (c->prec < 0) return fail(CHYM_ESTATE, "no state");
+  CHYM_CUDA_TRY(cudaMemcpyAsync(d_koff_out, c->d_koff, sizeof(int64_t) * c->n_runs,
+                                cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return CHYM_OK;
 }
 
@@ -440,6 +465,7 @@ chym_status chym_set_state(chym_ctx* c, const double* X, int n_runs, const doubl
   CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_h, h, sizeof(double) * n_h, cudaMemcpyHostToDevice, st));
   CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_seeds, seeds, sizeof(uint64_t) * n_runs,
                                 cudaMemcpyHostToDevice, st));
+  CHYM_CUDA_TRY(cudaMemsetAsync(c->d_koff, 0, sizeof(int64_t) * n_runs, st));
   CHYM_CUDA_TRY(cudaStreamSynchronize(st));
   c->prec = prec;
   c->k = k;

@@ -57,6 +57,7 @@ struct K2Desc {
   uint8_t* Xt;           // both buffers; buffer b at Xt + b * buf_bytes
   const float* ar;       // per run: 1 + dt (h - 1)
   const uint4* rk;       // per run: Philox round keys [5]
+  const int64_t* koff;   // per run: global step of its (re)seeding
   unsigned long long buf_bytes;
   int N, KP, MT, KC, CT, n_runs, a_terms, sched_kind;
   int64_t k0, k_anneal, k_total;  // k0: step of the context when the call began
@@ -326,12 +327,6 @@ __global__ void __launch_bounds__(kThreads, 2) step_k2_kernel(K2Launch L) {
     const int kl = i_loc & 63;
     const uint32_t k_off = (uint32_t)(kl & 7) * 2u + (uint32_t)(kl >> 3) * kLboB;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    float ramp = 1.f;
-    if (d.sched_kind == 1 && k >= d.k_anneal)
-      ramp = k >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(k - d.k_anneal) * d.inv_ramp);
-    float e_mu[D];
-#pragma unroll
-    for (int mu = 0; mu < D; ++mu) e_mu[mu] = d.edt * (mu == 0 ? 1.f : ramp);
     if (ok) {
       for (int i = 0; i < runs_half; ++i) {
         const int c0 = c_begin + i * D;
@@ -346,6 +341,11 @@ __global__ void __launch_bounds__(kThreads, 2) step_k2_kernel(K2Launch L) {
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) xn[mu] = 0.f;
         if (live && run < d.n_runs) {
+          // the run's local step: noise counter and annealing scale alpha_mu
+          const int64_t kl = k - __ldg(d.koff + run);
+          float ramp = 1.f;
+          if (d.sched_kind == 1 && kl >= d.k_anneal)
+            ramp = kl >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(kl - d.k_anneal) * d.inv_ramp);
           float n2 = 0.f;
 #pragma unroll
           for (int mu = 0; mu < D; ++mu) n2 = fmaf(xa[mu], xa[mu], n2);
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 2) step_k2_kernel(K2Launch L) {
           float z[4 * ((D + 3) / 4)];
 #pragma unroll
           for (int blk = 0; blk < (D + 3) / 4; ++blk) {
-            const uint4 w = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)k),
+            const uint4 w = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)kl),
                                       d.rk + (size_t)run * 5);
             box_muller(w.x, w.y, d.neg2ln2s2, z[4 * blk], z[4 * blk + 1]);
             if (D - 4 * blk > 2) box_muller(w.z, w.w, d.neg2ln2s2, z[4 * blk + 2], z[4 * blk + 3]);
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 2) step_k2_kernel(K2Launch L) {
 #pragma unroll
           for (int mu = 0; mu < D; ++mu) {
             const float s = fmaf(-d.kdt * xa[mu], xa[mu], t);
-            xn[mu] = fmaf(xa[mu], s, fmaf(e_mu[mu], y[mu], z[mu]));
+            xn[mu] = fmaf(xa[mu], s, fmaf(d.edt * (mu == 0 ? 1.f : ramp), y[mu], z[mu]));
             d.Xm[(size_t)(c_glob + mu) * d.KP + p] = xn[mu];
           }
         }
@@ -508,6 +508,7 @@ cudaError_t k2_prepare_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st,
   d.Xt = Xt;
   d.ar = ar;
   d.rk = rk;
+  d.koff = c->d_koff;
   d.buf_bytes = (unsigned long long)(2 * CT * KC * BB);
   d.N = N;
   d.KP = KP;

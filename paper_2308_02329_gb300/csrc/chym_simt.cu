@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg
   const T* Jsrc = J_SMEM ? Js : Jg;
 
   const T dt = (T)sc.dt, gamma = (T)sc.gamma, kappa = (T)sc.kappa;
+  const T inv_ramp = sc.sched_kind == 1 ? T(1) / (T)(sc.k_total - sc.k_anneal) : T(0);
   const int n_groups = RC / RB;
   for (int64_t k = sc.k0; k < sc.k0 + sc.steps; ++k) {
     // ---- phase A: coupling product, RB runs per thread ----
@@ -116,13 +117,16 @@ __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg
         for (int mu = 0; mu < D; ++mu) Ys[((size_t)(g * RB + b) * N + p) * D + mu] = acc[b][mu];
     }
     __syncthreads();
-    // ---- phase B: local drift, annealing and noise ----
-    T ea[D];
-#pragma unroll
-    for (int mu = 0; mu < D; ++mu)
-      ea[mu] = (T)(sc.eps * alpha_of(sc.sched_kind, k, sc.k_anneal, sc.k_total, mu));
+    // ---- phase B: local drift, annealing and noise (at each run's local step) ----
     for (int s = tid; s < nr * N; s += nt) {
       const int rl = s / N, p = s % N, run = run0 + rl;
+      const int64_t kl = k - sc.koff[run];
+      T ramp = T(1);  // alpha_mu(kl) for mu >= 1; mu = 0 keeps alpha = 1
+      if (sc.sched_kind == 1 && kl >= sc.k_anneal)
+        ramp = kl >= sc.k_total ? T(0) : T(1) - (T)(kl - sc.k_anneal) * inv_ramp;
+      T ea[D];
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) ea[mu] = (T)sc.eps * (mu == 0 ? T(1) : ramp);
       const T hm1 = (T)(hg[run / sc.replicas] - 1.0);
       T* x = Xs + (size_t)s * D;
       const T* y = Ys + (size_t)s * D;
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg
 #pragma unroll
       for (int mu = 0; mu < D; ++mu) n2 = fma(x[mu], x[mu], n2);
       T z[D];
-      spin_normals<T, D>(seeds[run], 0u, (uint64_t)k, p, (T)sc.noise_scale, z);
+      spin_normals<T, D>(seeds[run], 0u, (uint64_t)kl, p, (T)sc.noise_scale, z);
 #pragma unroll
       for (int mu = 0; mu < D; ++mu) {
         const T xm = x[mu];
@@ -210,7 +214,57 @@ cudaError_t launch_init_typed(chym_ctx* c, cudaStream_t st, double init_std) {
   return cudaGetLastError();
 }
 
+// Reinitialise the listed runs from new seeds at local step 0 (offset = current k).
+template <typename T, int D>
+__global__ void reseed_kernel(T* __restrict__ X, uint64_t* __restrict__ seeds, int64_t* __restrict__ koff,
+                              const int32_t* __restrict__ runs, int n, const uint64_t* __restrict__ new_seeds,
+                              int N, int64_t k_now, T init_std) {
+  const int64_t total = (int64_t)n * N;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(s / N), p = (int)(s % N);
+    const int run = runs[i];
+    const uint64_t sd = new_seeds[i];
+    T z[D];
+    spin_normals<T, D>(sd, 1u, 0ull, p, init_std, z);
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) X[((int64_t)run * N + p) * D + mu] = z[mu];
+    if (p == 0) {
+      seeds[run] = sd;
+      koff[run] = k_now;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_reseed_typed(chym_ctx* c, const int32_t* runs, int n, const uint64_t* ns,
+                                double init_std, cudaStream_t st) {
+  const int threads = 256;
+  const int grid = (int)std::min<int64_t>(((int64_t)n * c->N + threads - 1) / threads, 152 * 16);
+  T* X = (T*)c->d_X;
+  switch (c->D) {
+#define CHYM_RESEED_CASE(DD)                                                                       \
+  case DD:                                                                                        \
+    reseed_kernel<T, DD><<<grid, threads, 0, st>>>(X, c->d_seeds, c->d_koff, runs, n, ns, c->N, c->k, \
+                                                  (T)init_std);                                    \
+    break;
+    CHYM_RESEED_CASE(1) CHYM_RESEED_CASE(2) CHYM_RESEED_CASE(3) CHYM_RESEED_CASE(4)
+    CHYM_RESEED_CASE(5) CHYM_RESEED_CASE(6) CHYM_RESEED_CASE(7) CHYM_RESEED_CASE(8)
+#undef CHYM_RESEED_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_reseed(chym_ctx* c, const int32_t* d_runs, int n, const uint64_t* d_new_seeds,
+                          double init_std, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (c->prec == CHYM_PREC_FP64)
+    return launch_reseed_typed<double>(c, d_runs, n, d_new_seeds, init_std, st);
+  return launch_reseed_typed<float>(c, d_runs, n, d_new_seeds, init_std, st);
+}
 
 cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st) {
   if (sc.steps <= 0 || sc.n_runs <= 0) return cudaSuccess;

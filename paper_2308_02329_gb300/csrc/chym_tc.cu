@@ -35,6 +35,7 @@ struct TcDesc {
   float* X;
   const double* h;
   const uint64_t* seeds;
+  const int64_t* koff;  // per run: global step of its (re)seeding
   int N, KP, n_runs, replicas, a_terms, sched_kind;
   int64_t k0, k_anneal, k_total;
   float dt, noise_scale, gdt, kdt, edt, inv_ramp;
@@ -286,6 +287,8 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
   __shared__ __align__(8) uint64_t s_abar;
   __shared__ __align__(8) float s_ar[G][RG];
   __shared__ uint4 s_rk[G][RG][5];  // Philox round keys of each run
+  __shared__ int64_t s_koff[G][RG];  // each run's (re)seeding step
+  __shared__ int s_kuni[G];           // 1 when all runs of the group share one offset
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = warp >> 2, wq = warp & 3;
@@ -358,15 +361,18 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
         k1 = (uint32_t)(sd >> 32);
       }
       s_ar[g][p] = ar;
+      s_koff[g][p] = p < nr ? d.koff[run] : 0;
       for (int i = 0; i < 5; ++i) {  // Weyl key schedule: round r uses key + r * (W0, W1)
         s_rk[g][p][i] = make_uint4(k0 + (2u * i) * kPhiloxW0, k1 + (2u * i) * kPhiloxW1,
                                    k0 + (2u * i + 1u) * kPhiloxW0, k1 + (2u * i + 1u) * kPhiloxW1);
       }
     }
+    if (p == 0) s_kuni[g] = 1;
     // zero the B operands (K padding rows and unused runs must stay finite zeros)
     for (uint32_t o = (uint32_t)(tid & 127) * 16u; o < 2u * b_bytes; o += 128u * 16u)
       *reinterpret_cast<uint4*>(Bhi + o) = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();  // every zero must land before any thread writes its state into B
+    if (p < nr && s_koff[g][p] != s_koff[g][0]) s_kuni[g] = 0;
     const bool live = p < N;
     // ---- load the state: X[run][p][mu] -> TMEM master + BF16 hi/lo B ----
     for (int r0 = 0; r0 < nr; r0 += CH) {
@@ -389,6 +395,8 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
     __syncthreads();
 
     // ---- step loop (each group independently) ----
+    const bool k_uniform = s_kuni[g] != 0;
+    const int64_t koff_u = s_koff[g][0];
     const uint32_t a_sbo = (uint32_t)(KP / 8) * 128u;
     const int ksteps = KP / 16;
     const float neg2ln2s2 = -1.3862943611198906f * d.noise_scale * d.noise_scale;
@@ -439,18 +447,11 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
           s_abort = 1;
         }
         tc_fence_after();
-        // per-step coupling scale dt eps alpha_mu(k)
-        float2 e_mu2[D];
-        {
-          float ramp = 1.f;
-          if (d.sched_kind == 1 && k >= d.k_anneal)
-            ramp = k >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(k - d.k_anneal) * d.inv_ramp);
-#pragma unroll
-          for (int mu = 0; mu < D; ++mu) {
-            const float e = d.edt * (mu == 0 ? 1.f : ramp);
-            e_mu2[mu] = make_float2(e, e);
-          }
-        }
+        // annealing scale when every run of the group shares one local step
+        float ramp_u = 1.f;
+        const int64_t kl_u = k - koff_u;
+        if (d.sched_kind == 1 && kl_u >= d.k_anneal)
+          ramp_u = kl_u >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(kl_u - d.k_anneal) * d.inv_ramp);
         if (ok) {
           for (int r0 = 0; r0 < nr; r0 += CH) {
             float x[D][CH], y[D][CH];
@@ -463,12 +464,28 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
               for (int j = 0; j < CH; j += 2) {  // two runs at once, FP32x2 arithmetic
                 const int r = r0 + j;
                 const float2 ar = *reinterpret_cast<const float2*>(&s_ar[g][r]);
+                // each run's local step: noise counter and annealing scale alpha_mu
+                int64_t klA = kl_u, klB = kl_u;
+                float rA = ramp_u, rB = ramp_u;
+                if (!k_uniform) {
+                  klA = k - s_koff[g][r];
+                  klB = k - s_koff[g][r + 1];
+                  rA = rB = 1.f;
+                }
+                if (!k_uniform && d.sched_kind == 1) {
+                  if (klA >= d.k_anneal)
+                    rA = klA >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(klA - d.k_anneal) * d.inv_ramp);
+                  if (klB >= d.k_anneal)
+                    rB = klB >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(klB - d.k_anneal) * d.inv_ramp);
+                }
+                const float2 e0 = make_float2(d.edt, d.edt), e1 = make_float2(d.edt * rA, d.edt * rB);
                 float2 z[4 * ((D + 3) / 4)];
 #pragma unroll
                 for (int blk = 0; blk < (D + 3) / 4; ++blk) {
-                  const uint4 c = noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)k);
-                  const uint4 wA = philox_rk(c, s_rk[g][r]);
-                  const uint4 wB = philox_rk(c, s_rk[g][r + 1]);
+                  const uint4 wA = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)klA),
+                                             s_rk[g][r]);
+                  const uint4 wB = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)klB),
+                                             s_rk[g][r + 1]);
                   box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, z[4 * blk], z[4 * blk + 1]);
                   if (D - 4 * blk > 2)
                     box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, z[4 * blk + 2], z[4 * blk + 3]);
@@ -484,7 +501,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
                 for (int mu = 0; mu < D; ++mu) {
                   const float2 q = __fmul2_rn(nkdt, xx[mu]);
                   const float2 sfac = __ffma2_rn(q, xx[mu], t);
-                  const float2 inner = __ffma2_rn(e_mu2[mu], make_float2(y[mu][j], y[mu][j + 1]), z[mu]);
+                  const float2 inner = __ffma2_rn(mu == 0 ? e0 : e1, make_float2(y[mu][j], y[mu][j + 1]), z[mu]);
                   const float2 xn = __ffma2_rn(xx[mu], sfac, inner);
                   x[mu][j] = xn.x;
                   x[mu][j + 1] = xn.y;
@@ -603,6 +620,7 @@ void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out) {
   d.X = (float*)c->d_X;
   d.h = c->d_h;
   d.seeds = c->d_seeds;
+  d.koff = c->d_koff;
   d.N = c->N;
   d.KP = (c->N + 15) / 16 * 16;
   d.n_runs = sc.n_runs;

@@ -480,3 +480,39 @@ def test_batch_many_small_instances_against_checker():
         assert _rel_err(X[pick], Xo) <= 1e-4
         c.close()
     batch.close()
+
+
+# ---------------------------------------------------------------------------
+# retire-and-reseed: a reseeded run follows the trajectory of a fresh run
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,D,prec,tol", [(24, 3, chym.PREC_FP64, 1e-10),
+                                          (100, 4, chym.PREC_BF16X2, 1e-4),
+                                          (150, 2, chym.PREC_BF16X2, 1e-4),
+                                          (40, 8, chym.PREC_FP32, 1e-4)])
+def test_reseeded_runs_restart_at_local_step_zero(N, D, prec, tol):
+    torch = pytest.importorskip("torch")
+    n_h, reps, K1, K2 = 2, 6, 40, 30
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 17)
+    prm = chym.Params(eps=eps, prec=prec)
+    sch = chym.Schedule(1, 35, 60)  # the ramp starts inside both segments
+    ctx = chym.Context(J, D)
+    ctx.run(prm, h, seeds, K1, sch)
+    picked = np.array([1, 3, 10], dtype=np.int32)
+    fresh = inputs.run_seeds(999, len(picked))
+    d_runs = torch.from_numpy(picked).cuda()
+    d_seeds = torch.from_numpy(fresh.view(np.int64)).cuda()
+    ctx.reseed_device(d_runs.data_ptr(), len(picked), d_seeds.data_ptr(), prm.init_std)
+    ctx.run(prm, None, None, K2, sch, n_runs=len(seeds))
+    X, k = ctx.get_state()
+    assert k == K1 + K2
+    offs = torch.zeros(len(seeds), dtype=torch.int64, device="cuda")
+    ctx.offsets_device(offs.data_ptr())
+    torch.cuda.synchronize()
+    assert offs.cpu().numpy().tolist() == [K1 if r in picked else 0 for r in range(len(seeds))]
+    hr = inputs.h_per_run(h, reps)
+    rest = np.array([r for r in range(len(seeds)) if r not in picked])
+    Xo_rest = O.run(J, D, hr[rest], seeds[rest], oracle_params(prm), oracle_schedule(sch), K1 + K2)
+    Xo_new = O.run(J, D, hr[picked], fresh, oracle_params(prm), oracle_schedule(sch), K2)
+    assert _rel_err(X[rest], Xo_rest) <= tol
+    assert _rel_err(X[picked], Xo_new) <= tol
+    ctx.close()
