@@ -234,6 +234,56 @@ CHYM_API chym_status chym_batch_status(chym_batch* b);
 
 CHYM_API chym_status chym_batch_destroy(chym_batch* b);
 
+/* ---- Learned early exit (no counterpart in the paper's method; a layer on top of
+ * it): features of a run's early trajectory and a 24-64-64-1 GELU network with
+ * BF16 weights and FP32 accumulation that predicts whether the run will end at
+ * the Ising ground state, so that runs judged doomed can be retired and their
+ * slots reseeded (chym_reseed_device). ---- */
+typedef struct chym_mlp chym_mlp;
+
+/* Copy the raw run state (the context's storage type: double for FP64, float
+ * otherwise; n_runs * N * D values, layout X[run][p][mu]) to device memory, e.g.
+ * to keep a snapshot for chym_features_device.  Asynchronous. */
+CHYM_API chym_status chym_copy_state_device(chym_ctx* ctx, void* d_dst, void* cuda_stream);
+
+/* 24 features per run into d_features (device float, n_runs x 24) from the current
+ * state and a snapshot taken earlier with chym_copy_state_device:
+ *  0-11  quantiles of |x_p0| / rms at levels j/11 (sorted order statistic
+ *        floor(j (N-1)/11 + 1/2)), rms = sqrt(mean_p x_p0^2);
+ *  12    E/N, Ising energy of the signs now (Eq. 3 with Ising spins);
+ *  13    (E - E_snapshot)/N;  14  extra-dimension weight sum_{mu>=1} x^2 / sum x^2;
+ *  15    its change since the snapshot;  16  fraction of spins whose sign flipped;
+ *  17    E_hs/N (Eq. 3);  18  mean |x_p|;  19  the run's pump h;  20  D/8;
+ *  21    ln N / ln 2048;  22  k_frac (fraction of the schedule reached);  23  rms.
+ * N <= 4096.  Asynchronous. */
+CHYM_API chym_status chym_features_device(chym_ctx* ctx, const void* d_snapshot, double k_frac,
+                                          float* d_features, void* cuda_stream);
+
+/* Network 24 -> 64 -> 64 -> 1: standardised input (f - mean) * istd, GELU hidden
+ * layers, logit output; 5825 FP32 master parameters laid out W1[64][24], b1[64],
+ * W2[64][64], b2[64], W3[64], b3, a BF16 copy of them used by the forward pass,
+ * and Adam moments.  Initialised Glorot-uniform from `seed`; max_batch bounds the
+ * training batch.  Synchronous. */
+CHYM_API chym_status chym_mlp_create(uint64_t seed, int max_batch, chym_mlp** out);
+CHYM_API chym_status chym_mlp_destroy(chym_mlp* net);
+/* Host parameter vector (5825 floats) and standardisation (24 + 24); any may be
+ * NULL to keep the current values.  Setting the parameters resets Adam. */
+CHYM_API chym_status chym_mlp_set_params(chym_mlp* net, const float* theta, const float* mean,
+                                         const float* istd);
+CHYM_API chym_status chym_mlp_get_params(chym_mlp* net, float* theta_out);
+/* Logits of B feature rows (device).  Asynchronous. */
+CHYM_API chym_status chym_mlp_forward_device(chym_mlp* net, const float* d_features, int B,
+                                             float* d_logits, void* cuda_stream);
+/* Gradient of the mean binary cross-entropy-with-logits over B rows with labels
+ * d_labels (device, 0 or 1) into d_grad (device, 5825, nullable) and the loss into
+ * d_loss (device, nullable).  B <= max_batch.  Asynchronous. */
+CHYM_API chym_status chym_mlp_grad_device(chym_mlp* net, const float* d_features, const float* d_labels,
+                                          int B, float* d_grad, float* d_loss, void* cuda_stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that gradient with learning rate lr. */
+CHYM_API chym_status chym_mlp_train_step_device(chym_mlp* net, const float* d_features,
+                                                const float* d_labels, int B, float lr,
+                                                float* d_loss, void* cuda_stream);
+
 /* ---- Statistics without device allocation ----
  * No counterpart in the paper: this entry point exists for callers that cannot
  * allocate device memory at the point where they need the statistics (a host

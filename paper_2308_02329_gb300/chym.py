@@ -26,7 +26,10 @@ EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", 
            "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
            "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
            "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
-           "chym_reseed_device", "chym_get_offsets_device"]
+           "chym_reseed_device", "chym_get_offsets_device", "chym_copy_state_device",
+           "chym_features_device", "chym_mlp_create", "chym_mlp_destroy", "chym_mlp_set_params",
+           "chym_mlp_get_params", "chym_mlp_forward_device", "chym_mlp_grad_device",
+           "chym_mlp_train_step_device"]
 
 
 class ChymError(RuntimeError):
@@ -111,6 +114,15 @@ def lib():
         L.chym_ground_state_search.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp]
         L.chym_reseed_device.argtypes = [vp, vp, i32, vp, dbl, vp]
         L.chym_get_offsets_device.argtypes = [vp, vp, vp]
+        L.chym_copy_state_device.argtypes = [vp, vp, vp]
+        L.chym_features_device.argtypes = [vp, vp, dbl, vp, vp]
+        L.chym_mlp_create.argtypes = [ctypes.c_uint64, i32, ctypes.POINTER(vp)]
+        L.chym_mlp_destroy.argtypes = [vp]
+        L.chym_mlp_set_params.argtypes = [vp, vp, vp, vp]
+        L.chym_mlp_get_params.argtypes = [vp, vp]
+        L.chym_mlp_forward_device.argtypes = [vp, vp, i32, vp, vp]
+        L.chym_mlp_grad_device.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.chym_mlp_train_step_device.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp]
         L.chym_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
         L.chym_batch_run.argtypes = [vp, ctypes.POINTER(CParams), ctypes.POINTER(CSchedule), i64, vp]
         L.chym_batch_status.argtypes = [vp]
@@ -234,6 +246,13 @@ class Context:
     def offsets_device(self, d_out, stream=0):
         _check(lib().chym_get_offsets_device(self._h, ctypes.c_void_p(d_out), ctypes.c_void_p(stream)))
 
+    def copy_state_device(self, d_dst, stream=0):
+        _check(lib().chym_copy_state_device(self._h, ctypes.c_void_p(d_dst), ctypes.c_void_p(stream)))
+
+    def features_device(self, d_snapshot, k_frac, d_features, stream=0):
+        _check(lib().chym_features_device(self._h, ctypes.c_void_p(d_snapshot), float(k_frac),
+                                          ctypes.c_void_p(d_features), ctypes.c_void_p(stream)))
+
     def get_state(self, stream=0):
         n_runs, _, _ = self.info()
         X = np.zeros((n_runs, self.N, self.D), dtype=np.float64)
@@ -254,6 +273,54 @@ def ground_state_mobius(N, j_ring=-1.0, j_rung=-1.0):
     e = ctypes.c_double()
     _check(lib().chym_ground_state_mobius(int(N), float(j_ring), float(j_rung), ctypes.byref(e)))
     return e.value
+
+
+N_MLP_PARAMS = 5825
+N_FEATURES = 24
+
+
+class MLP:
+    """The early-exit network (see chym_mlp_* in include/chym.h)."""
+
+    def __init__(self, seed=1, max_batch=4096):
+        h = ctypes.c_void_p()
+        _check(lib().chym_mlp_create(int(seed), int(max_batch), ctypes.byref(h)))
+        self._h = h
+
+    def set_params(self, theta=None, mean=None, istd=None):
+        f = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+        theta, mean, istd = f(theta), f(mean), f(istd)
+        _check(lib().chym_mlp_set_params(self._h, _ptr(theta), _ptr(mean), _ptr(istd)))
+
+    def get_params(self):
+        out = np.zeros(N_MLP_PARAMS, dtype=np.float32)
+        _check(lib().chym_mlp_get_params(self._h, _ptr(out)))
+        return out
+
+    def forward_device(self, d_F, B, d_logits, stream=0):
+        _check(lib().chym_mlp_forward_device(self._h, ctypes.c_void_p(d_F), int(B),
+                                             ctypes.c_void_p(d_logits), ctypes.c_void_p(stream)))
+
+    def grad_device(self, d_F, d_y, B, d_grad=0, d_loss=0, stream=0):
+        _check(lib().chym_mlp_grad_device(self._h, ctypes.c_void_p(d_F), ctypes.c_void_p(d_y), int(B),
+                                          ctypes.c_void_p(d_grad), ctypes.c_void_p(d_loss),
+                                          ctypes.c_void_p(stream)))
+
+    def train_step_device(self, d_F, d_y, B, lr, d_loss=0, stream=0):
+        _check(lib().chym_mlp_train_step_device(self._h, ctypes.c_void_p(d_F), ctypes.c_void_p(d_y),
+                                                int(B), float(lr), ctypes.c_void_p(d_loss),
+                                                ctypes.c_void_p(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().chym_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
