@@ -172,11 +172,13 @@ CHYM_API chym_status chym_set_state(chym_ctx* ctx, const double* X, int n_runs, 
  * runs continue: x(0) = init_std * N(0,1) from the new key (tag 1), and from then
  * on the run's noise counter and annealing schedule use its local step
  * k - k_reseed (k_reseed = the context's current step).  A reseeded run therefore
- * follows exactly the trajectory of a fresh run with that seed.  Asynchronous;
- * listed runs must be distinct and < n_runs. */
+ * follows exactly the trajectory of a fresh run with that seed.  d_new_pump
+ * (device int32, nullable) gives each restarted run a new index into h (default:
+ * keep its pump); chym_stats counts every run under its current pump.
+ * Asynchronous; listed runs must be distinct and < n_runs. */
 CHYM_API chym_status chym_reseed_device(chym_ctx* ctx, const int32_t* d_runs, int n,
-                                        const uint64_t* d_new_seeds, double init_std,
-                                        void* cuda_stream);
+                                        const uint64_t* d_new_seeds, const int32_t* d_new_pump,
+                                        double init_std, void* cuda_stream);
 
 /* Per-run (re)seeding steps (device int64, n_runs): the local step of run r at the
  * context's step k is k - offsets[r].  Asynchronous. */

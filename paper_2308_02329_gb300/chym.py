@@ -112,7 +112,7 @@ def lib():
         L.chym_ground_state_exact.argtypes = [vp, ctypes.POINTER(dbl), vp]
         L.chym_ground_state_mobius.argtypes = [i32, dbl, dbl, ctypes.POINTER(dbl)]
         L.chym_ground_state_search.argtypes = [vp, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp]
-        L.chym_reseed_device.argtypes = [vp, vp, i32, vp, dbl, vp]
+        L.chym_reseed_device.argtypes = [vp, vp, i32, vp, vp, dbl, vp]
         L.chym_get_offsets_device.argtypes = [vp, vp, vp]
         L.chym_copy_state_device.argtypes = [vp, vp, vp]
         L.chym_features_device.argtypes = [vp, vp, dbl, vp, vp]
@@ -237,11 +237,12 @@ class Context:
                                               ctypes.byref(e), _ptr(S)))
         return e.value, unpack_spins(S, self.N)[0]
 
-    def reseed_device(self, d_runs, n, d_new_seeds, init_std, stream=0):
-        """Restart the n runs listed at device address d_runs (int32) from new seeds."""
+    def reseed_device(self, d_runs, n, d_new_seeds, init_std, d_new_pump=0, stream=0):
+        """Restart the n runs listed at device address d_runs (int32) from new seeds,
+        optionally with new pump indices (device int32)."""
         _check(lib().chym_reseed_device(self._h, ctypes.c_void_p(d_runs), int(n),
-                                        ctypes.c_void_p(d_new_seeds), float(init_std),
-                                        ctypes.c_void_p(stream)))
+                                        ctypes.c_void_p(d_new_seeds), ctypes.c_void_p(d_new_pump),
+                                        float(init_std), ctypes.c_void_p(stream)))
 
     def offsets_device(self, d_out, stream=0):
         _check(lib().chym_get_offsets_device(self._h, ctypes.c_void_p(d_out), ctypes.c_void_p(stream)))

@@ -70,6 +70,7 @@ chym_status ensure_batch(chym_ctx* c, int n_runs, int n_h) {
     free_dev(c->d_X);
     free_dev(c->d_seeds);
     free_dev(c->d_koff);
+    free_dev(c->d_hidx);
     free_dev(c->d_E);
     free_dev(c->d_spins);
     c->cap_runs = 0;
@@ -78,6 +79,7 @@ chym_status ensure_batch(chym_ctx* c, int n_runs, int n_h) {
     CHYM_CUDA_TRY(cudaMalloc(&c->d_X, xb));
     CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_seeds, sizeof(uint64_t) * n_runs));
     CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_koff, sizeof(int64_t) * n_runs));
+    CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_hidx, sizeof(int32_t) * n_runs));
     CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_E, sizeof(double) * n_runs));
     CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_spins, sizeof(uint64_t) * (size_t)n_runs * words));
     c->x_bytes = xb;
@@ -112,6 +114,7 @@ StepConsts make_step_consts(const chym_ctx* c, const chym_params* prm, const chy
   sc.k_anneal = s->k_anneal;
   sc.k_total = s->k_total;
   sc.koff = c->d_koff;
+  sc.hidx = c->d_hidx;
   return sc;
 }
 
@@ -124,6 +127,7 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
     c->prec = prm->prec;
     c->k = 0;
     CHYM_CUDA_TRY(cudaMemsetAsync(c->d_koff, 0, sizeof(int64_t) * c->n_runs, st));
+    CHYM_CUDA_TRY(launch_fill_hidx(c->d_hidx, c->n_runs, c->n_runs / c->n_h, st));
     CHYM_CUDA_TRY(launch_init(c, c->prec, st, prm->init_std));
   } else if (prm->prec != c->prec) {
     // FP32 and BF16X2 share FP32 storage; FP64 storage cannot be continued in
@@ -255,6 +259,7 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_h);
   free_dev(c->d_seeds);
   free_dev(c->d_koff);
+  free_dev(c->d_hidx);
   free_dev(c->d_E);
   free_dev(c->d_spins);
   free_dev(c->d_status);
@@ -275,13 +280,13 @@ chym_status chym_lambda_max(chym_ctx* c, double* out) {
 }
 
 chym_status chym_reseed_device(chym_ctx* c, const int32_t* d_runs, int n, const uint64_t* d_new_seeds,
-                               double init_std, void* stream) {
+                               const int32_t* d_new_pump, double init_std, void* stream) {
   if (!c) return fail(CHYM_EINVAL, "ctx is NULL");
   if (c->prec < 0) return fail(CHYM_ESTATE, "no state: call chym_run first");
   if (n < 0 || (n > 0 && (!d_runs || !d_new_seeds))) return fail(CHYM_EINVAL, "bad run list");
   if (!(init_std >= 0.0) || !isfinite(init_std)) return fail(CHYM_EINVAL, "init_std must be >= 0");
   if (n == 0) return CHYM_OK;
-  CHYM_CUDA_TRY(launch_reseed(c, d_runs, n, d_new_seeds, init_std, (cudaStream_t)stream));
+  CHYM_CUDA_TRY(launch_reseed(c, d_runs, n, d_new_seeds, d_new_pump, init_std, (cudaStream_t)stream));
   c->have_energy = false;
   return CHYM_OK;
 }
@@ -391,7 +396,7 @@ chym_status chym_stats(chym_ctx* c, double E_gs, chym_stats_t* out, int64_t* hit
   const double tol = pm1 ? 0.0 : 1e-9 * fabs(E_gs);
   double bin_w = pm1 ? 4.0 : 1e-3 * fabs(E_gs);
   if (!(bin_w > 0.0)) bin_w = 1.0;
-  CHYM_CUDA_TRY(launch_stats(c, c->d_E, E_gs, tol, bin_w, n_bins, c->d_scratch, st));
+  CHYM_CUDA_TRY(launch_stats(c, c->d_E, E_gs, tol, bin_w, n_bins, c->d_scratch, st));  // per-run pumps
   std::vector<unsigned char> buf(need);
   CHYM_CUDA_TRY(cudaMemcpyAsync(buf.data(), c->d_scratch, need, cudaMemcpyDeviceToHost, st));
   CHYM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -466,6 +471,7 @@ chym_status chym_set_state(chym_ctx* c, const double* X, int n_runs, const doubl
   CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_seeds, seeds, sizeof(uint64_t) * n_runs,
                                 cudaMemcpyHostToDevice, st));
   CHYM_CUDA_TRY(cudaMemsetAsync(c->d_koff, 0, sizeof(int64_t) * n_runs, st));
+  CHYM_CUDA_TRY(launch_fill_hidx(c->d_hidx, n_runs, n_runs / n_h, st));
   CHYM_CUDA_TRY(cudaStreamSynchronize(st));
   c->prec = prec;
   c->k = k;

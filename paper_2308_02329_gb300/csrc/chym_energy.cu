@@ -98,6 +98,7 @@ struct StatsOut {
 constexpr int kStatsThreads = 1024;
 
 __global__ void __launch_bounds__(kStatsThreads) stats_kernel(const double* __restrict__ E,
+                                                              const int32_t* __restrict__ hidx,
                                                               int n_runs, int replicas, int n_h,
                                                               double E_gs, double tol,
                                                               double bin_w, int n_bins,
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(const double* __re
     sum += e - E_gs;
     const bool hit = fabs(e - E_gs) <= tol;
     if (hit) {
-      atomicAdd(&sh_hits[r / replicas], 1ull);
+      atomicAdd(&sh_hits[hidx ? hidx[r] : r / replicas], 1ull);
       ++nh;
     }
     if (e < be || (e == be && r < br)) { be = e; br = r; }
@@ -195,7 +196,7 @@ cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<1, kStatsThreads, smem, st>>>(d_E, c->n_runs, c->n_runs / c->n_h, c->n_h, E_gs, tol,
+  kern<<<1, kStatsThreads, smem, st>>>(d_E, c->d_hidx, c->n_runs, c->n_runs / c->n_h, c->n_h, E_gs, tol,
                                        bin_w, n_bins, (StatsOut*)d_out);
   return cudaGetLastError();
 }
@@ -271,7 +272,7 @@ extern "C" CHYM_API chym_status chym_stats_noalloc(const double* d_E, int n_runs
   // the kernel initialises every word it reports (hits, bins, totals), so the
   // previous call's contents never leak into this one
   stats_kernel<<<1, kStatsThreads, sizeof(unsigned long long) * (size_t)n_h, st>>>(
-      d_E, n_runs, n_runs / n_h, n_h, E_gs, tol, bin_w, n_bins, (StatsOut*)scratch);
+      d_E, nullptr, n_runs, n_runs / n_h, n_h, E_gs, tol, bin_w, n_bins, (StatsOut*)scratch);
   CHYM_CUDA_TRY(cudaGetLastError());
   StatsOut head;
   CHYM_CUDA_TRY(cudaMemcpyAsync(&head, scratch, sizeof(head), cudaMemcpyDeviceToHost, st));

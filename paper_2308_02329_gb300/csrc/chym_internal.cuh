@@ -39,6 +39,7 @@ struct StepConsts {
   int sched_kind;             // 0 none, 1 linear
   int64_t k_anneal, k_total;
   const int64_t* koff;        // per run: global step at which the run was (re)seeded
+  const int32_t* hidx;        // per run: index of its pump value in h
 };
 
 // Device status word: bit flags raised by kernels, read back by the host.
@@ -153,6 +154,7 @@ struct chym_ctx {
   double* d_h = nullptr;
   uint64_t* d_seeds = nullptr;
   int64_t* d_koff = nullptr;  // per run: global step of its (re)seeding; local step = k - koff
+  int32_t* d_hidx = nullptr;  // per run: index of its pump value (run / replicas unless reseeded)
   double* d_E = nullptr;      // energies of the last chym_energy*
   uint64_t* d_spins = nullptr;
   bool have_energy = false;
@@ -171,7 +173,8 @@ namespace chym {
 // kernel launchers (implemented in the .cu files)
 cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_std);
 cudaError_t launch_reseed(chym_ctx* c, const int32_t* d_runs, int n, const uint64_t* d_new_seeds,
-                          double init_std, cudaStream_t st);
+                          const int32_t* d_new_hidx, double init_std, cudaStream_t st);
+cudaError_t launch_fill_hidx(int32_t* hidx, int n_runs, int replicas, cudaStream_t st);
 cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st);
 cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 cudaError_t launch_step_k2(chym_ctx* c, const StepConsts& sc, cudaStream_t st);

@@ -448,10 +448,11 @@ __global__ void k2_unpack_kernel(const float* __restrict__ Xm, float* __restrict
 }
 
 // per-run constants: 1 + dt (h - 1) and the ten Philox round keys
-__global__ void k2_runconst_kernel(const double* __restrict__ h, const uint64_t* __restrict__ seeds,
-                                   int n_runs, int replicas, double dt, float* ar, uint4* rk) {
+__global__ void k2_runconst_kernel(const double* __restrict__ h, const int32_t* __restrict__ hidx,
+                                   const uint64_t* __restrict__ seeds, int n_runs, double dt, float* ar,
+                                   uint4* rk) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_runs; r += gridDim.x * blockDim.x) {
-    ar[r] = (float)(1.0 + dt * (h[r / replicas] - 1.0));
+    ar[r] = (float)(1.0 + dt * (h[hidx[r]] - 1.0));
     const uint32_t k0 = (uint32_t)seeds[r], k1 = (uint32_t)(seeds[r] >> 32);
     for (int i = 0; i < 5; ++i)
       rk[(size_t)r * 5 + i] = make_uint4(k0 + (2u * i) * kPhiloxW0, k1 + (2u * i) * kPhiloxW1,
@@ -500,8 +501,8 @@ cudaError_t k2_prepare_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st,
   uint4* rk = (uint4*)((uint8_t*)ar + ar_bytes);
   cudaError_t e = cudaMemsetAsync(Xt, 0, xt_bytes, st);
   if (e != cudaSuccess) return e;
-  k2_runconst_kernel<<<(sc.n_runs + 255) / 256, 256, 0, st>>>(c->d_h, c->d_seeds, sc.n_runs,
-                                                             sc.replicas, sc.dt, ar, rk);
+  k2_runconst_kernel<<<(sc.n_runs + 255) / 256, 256, 0, st>>>(c->d_h, c->d_hidx, c->d_seeds,
+                                                             sc.n_runs, sc.dt, ar, rk);
   k2_pack_kernel<D><<<152 * 8, 256, 0, st>>>((const float*)c->d_X, Xm, Xt, N, KP, KC, CT, sc.n_runs);
   d.Aimg = (const uint8_t*)c->d_Ak2;
   d.Xm = Xm;

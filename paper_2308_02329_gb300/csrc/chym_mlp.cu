@@ -59,7 +59,7 @@ template <typename T, bool PM1>
 __global__ void __launch_bounds__(kFeatThreads) features_kernel(
     const T* __restrict__ X, const T* __restrict__ Xs, int N, int D, int P2,
     const int8_t* __restrict__ J8, const double* __restrict__ J64, const double* __restrict__ h,
-    int replicas, float k_frac, float* __restrict__ F) {
+    const int32_t* __restrict__ hidx, float k_frac, float* __restrict__ F) {
   extern __shared__ float sm[];
   float* buf = sm;                         // P2 floats: sort buffer, then sigma_mu
   float* inv = buf + P2;                   // N floats: 1/|x_p|
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kFeatThreads) features_kernel(
     o[16] = flips / (float)N;
     o[17] = ehs / (float)N;
     o[18] = sabs / (float)N;
-    o[19] = (float)h[run / replicas];
+    o[19] = (float)h[hidx[run]];
     o[20] = (float)D / 8.f;
     o[21] = logf((float)N) / logf(2048.f);
     o[22] = k_frac;
@@ -402,19 +402,18 @@ cudaError_t launch_features_typed(chym_ctx* c, const void* snap, double k_frac, 
   int P2 = 1;
   while (P2 < c->N) P2 <<= 1;
   const size_t smem = sizeof(float) * ((size_t)P2 + c->N) + 2 * (size_t)c->N + 16;
-  const int replicas = c->n_runs / c->n_h;
   if (c->kind == CHYM_J_PM1) {
     auto kern = features_kernel<T, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<c->n_runs, kFeatThreads, smem, st>>>((const T*)c->d_X, (const T*)snap, c->N, c->D, P2,
-                                                c->d_J8, c->d_J64, c->d_h, replicas, (float)k_frac, F);
+                                                c->d_J8, c->d_J64, c->d_h, c->d_hidx, (float)k_frac, F);
   } else {
     auto kern = features_kernel<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<c->n_runs, kFeatThreads, smem, st>>>((const T*)c->d_X, (const T*)snap, c->N, c->D, P2,
-                                                c->d_J8, c->d_J64, c->d_h, replicas, (float)k_frac, F);
+                                                c->d_J8, c->d_J64, c->d_h, c->d_hidx, (float)k_frac, F);
   }
   return cudaGetLastError();
 }

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg
       T ea[D];
 #pragma unroll
       for (int mu = 0; mu < D; ++mu) ea[mu] = (T)sc.eps * (mu == 0 ? T(1) : ramp);
-      const T hm1 = (T)(hg[run / sc.replicas] - 1.0);
+      const T hm1 = (T)(hg[sc.hidx[run]] - 1.0);
       T* x = Xs + (size_t)s * D;
       const T* y = Ys + (size_t)s * D;
       T n2 = T(0);
@@ -215,9 +215,15 @@ cudaError_t launch_init_typed(chym_ctx* c, cudaStream_t st, double init_std) {
 }
 
 // Reinitialise the listed runs from new seeds at local step 0 (offset = current k).
+__global__ void fill_hidx_kernel(int32_t* hidx, int n_runs, int replicas) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_runs; r += gridDim.x * blockDim.x)
+    hidx[r] = r / replicas;
+}
+
 template <typename T, int D>
 __global__ void reseed_kernel(T* __restrict__ X, uint64_t* __restrict__ seeds, int64_t* __restrict__ koff,
-                              const int32_t* __restrict__ runs, int n, const uint64_t* __restrict__ new_seeds,
+                              int32_t* __restrict__ hidx, const int32_t* __restrict__ runs, int n,
+                              const uint64_t* __restrict__ new_seeds, const int32_t* __restrict__ new_hidx,
                               int N, int64_t k_now, T init_std) {
   const int64_t total = (int64_t)n * N;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
@@ -232,21 +238,22 @@ __global__ void reseed_kernel(T* __restrict__ X, uint64_t* __restrict__ seeds, i
     if (p == 0) {
       seeds[run] = sd;
       koff[run] = k_now;
+      if (new_hidx) hidx[run] = new_hidx[i];
     }
   }
 }
 
 template <typename T>
 cudaError_t launch_reseed_typed(chym_ctx* c, const int32_t* runs, int n, const uint64_t* ns,
-                                double init_std, cudaStream_t st) {
+                                const int32_t* nh, double init_std, cudaStream_t st) {
   const int threads = 256;
   const int grid = (int)std::min<int64_t>(((int64_t)n * c->N + threads - 1) / threads, 152 * 16);
   T* X = (T*)c->d_X;
   switch (c->D) {
 #define CHYM_RESEED_CASE(DD)                                                                       \
   case DD:                                                                                        \
-    reseed_kernel<T, DD><<<grid, threads, 0, st>>>(X, c->d_seeds, c->d_koff, runs, n, ns, c->N, c->k, \
-                                                  (T)init_std);                                    \
+    reseed_kernel<T, DD><<<grid, threads, 0, st>>>(X, c->d_seeds, c->d_koff, c->d_hidx, runs, n, ns, nh, \
+                                                  c->N, c->k, (T)init_std);                        \
     break;
     CHYM_RESEED_CASE(1) CHYM_RESEED_CASE(2) CHYM_RESEED_CASE(3) CHYM_RESEED_CASE(4)
     CHYM_RESEED_CASE(5) CHYM_RESEED_CASE(6) CHYM_RESEED_CASE(7) CHYM_RESEED_CASE(8)
@@ -259,11 +266,17 @@ cudaError_t launch_reseed_typed(chym_ctx* c, const int32_t* runs, int n, const u
 }  // namespace
 
 cudaError_t launch_reseed(chym_ctx* c, const int32_t* d_runs, int n, const uint64_t* d_new_seeds,
-                          double init_std, cudaStream_t st) {
+                          const int32_t* d_new_hidx, double init_std, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (c->prec == CHYM_PREC_FP64)
-    return launch_reseed_typed<double>(c, d_runs, n, d_new_seeds, init_std, st);
-  return launch_reseed_typed<float>(c, d_runs, n, d_new_seeds, init_std, st);
+    return launch_reseed_typed<double>(c, d_runs, n, d_new_seeds, d_new_hidx, init_std, st);
+  return launch_reseed_typed<float>(c, d_runs, n, d_new_seeds, d_new_hidx, init_std, st);
+}
+
+cudaError_t launch_fill_hidx(int32_t* hidx, int n_runs, int replicas, cudaStream_t st) {
+  if (n_runs <= 0) return cudaSuccess;
+  fill_hidx_kernel<<<(n_runs + 255) / 256, 256, 0, st>>>(hidx, n_runs, replicas);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st) {

@@ -36,6 +36,7 @@ struct TcDesc {
   const double* h;
   const uint64_t* seeds;
   const int64_t* koff;  // per run: global step of its (re)seeding
+  const int32_t* hidx;  // per run: index of its pump value
   int N, KP, n_runs, replicas, a_terms, sched_kind;
   int64_t k0, k_anneal, k_total;
   float dt, noise_scale, gdt, kdt, edt, inv_ramp;
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
       float ar = 0.f;
       uint32_t k0 = 0u, k1 = 0u;
       if (p < nr) {
-        ar = (float)(1.0 + (double)d.dt * (d.h[run / d.replicas] - 1.0));
+        ar = (float)(1.0 + (double)d.dt * (d.h[d.hidx[run]] - 1.0));
         const uint64_t sd = d.seeds[run];
         k0 = (uint32_t)sd;
         k1 = (uint32_t)(sd >> 32);
@@ -621,6 +622,7 @@ void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out) {
   d.h = c->d_h;
   d.seeds = c->d_seeds;
   d.koff = c->d_koff;
+  d.hidx = c->d_hidx;
   d.N = c->N;
   d.KP = (c->N + 15) / 16 * 16;
   d.n_runs = sc.n_runs;

@@ -1,0 +1,179 @@
+"""Learned early exit: train the run-outcome network on trajectories the simulator
+generates, pick a retire threshold, and integrate with retire-and-reseed.
+
+Orchestration only: every step of the simulation, the features, the network's
+forward and backward passes and the Adam updates run in the CUDA library
+(through ``chym``); this module moves device pointers, shuffles mini-batch
+indices and keeps counts.  PyTorch provides device buffers and index shuffling.
+
+Schedule of one run: K steps, decision at local step k_dec (a divisor of K), with
+a state snapshot at k_dec / 2 for the slope features.  In continuous mode every
+slot of a context is always busy: the integration advances in chunks of k_dec
+steps; after each chunk, slots that reached their decision step are scored and
+retired when the logit is below the threshold, slots that reached K are harvested
+(their Ising energy decides a ground-state hit), and both kinds restart from fresh
+seeds (chym_reseed_device), so their local step starts again at 0.
+"""
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import chym, inputs
+
+
+@dataclass
+class Outcome:
+    hits: int = 0
+    completed: int = 0
+    retired: int = 0
+    run_steps: int = 0      # integration steps spent over all slots
+    seconds: float = 0.0
+
+    @property
+    def hits_per_mstep(self):
+        return 1e6 * self.hits / max(self.run_steps, 1)
+
+    @property
+    def hits_per_second(self):
+        return self.hits / max(self.seconds, 1e-12)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class SeedStream:
+    """Fresh 64-bit run seeds from a SplitMix64 stream of one key."""
+
+    def __init__(self, key):
+        self.key = int(key)
+        self.next = 0
+
+    def take(self, n):
+        out = inputs.run_seeds(self.key, n, offset=self.next)
+        self.next += n
+        return out
+
+
+def generate(ctx, prm, sched, h, seeds, K, k_dec, E_gs, stream=0):
+    """Run every seed to its decision step, record its features, finish it, label it.
+
+    Returns (features [R, 24] device float32, labels [R] device float32, energies
+    [R] host float64)."""
+    torch = _torch()
+    R = len(seeds)
+    ctx.run(prm, h, seeds, k_dec // 2, sched, stream)
+    el = ctx.N * ctx.D * R
+    snap = torch.empty(el, dtype=torch.float64 if prm.prec == chym.PREC_FP64 else torch.float32,
+                       device="cuda")
+    ctx.copy_state_device(snap.data_ptr(), stream)
+    ctx.run(prm, None, None, k_dec - k_dec // 2, sched, stream, n_runs=R)
+    F = torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda")
+    ctx.features_device(snap.data_ptr(), k_dec / K, F.data_ptr(), stream)
+    ctx.run(prm, None, None, K - k_dec, sched, stream, n_runs=R)
+    E = ctx.energy(stream=stream)
+    y = torch.from_numpy((np.abs(E - E_gs) <= 1e-9 * max(1.0, abs(E_gs))).astype(np.float32)).cuda()
+    return F, y, E
+
+
+def standardisation(F):
+    """Per-feature mean and inverse standard deviation of the training rows."""
+    mean = F.mean(0)
+    istd = 1.0 / F.std(0).clamp_min(1e-6)
+    return mean.cpu().numpy(), istd.cpu().numpy()
+
+
+def train(net, F, y, epochs=30, batch=512, lr=2e-3, seed=0, stream=0):
+    """Mini-batch Adam on the GPU; returns the mean loss of the last epoch."""
+    torch = _torch()
+    mean, istd = standardisation(F)
+    net.set_params(None, mean, istd)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    R = F.shape[0]
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for _ in range(epochs):
+        perm = torch.randperm(R, generator=g).cuda()
+        Fp, yp = F[perm].contiguous(), y[perm].contiguous()
+        for b0 in range(0, R - batch + 1, batch):
+            net.train_step_device(Fp[b0:].data_ptr(), yp[b0:].data_ptr(), batch, lr, loss.data_ptr(),
+                                  stream)
+        torch.cuda.synchronize()
+    return float(loss.item())
+
+
+def logits(net, F, stream=0):
+    torch = _torch()
+    out = torch.empty(F.shape[0], dtype=torch.float32, device="cuda")
+    net.forward_device(F.data_ptr(), F.shape[0], out.data_ptr(), stream)
+    return out
+
+
+def threshold_for_fn(scores, labels, fn_target):
+    """Largest threshold whose false-negative rate (successful runs scored below it)
+    stays at or below fn_target."""
+    pos = np.sort(scores[labels > 0.5])
+    if len(pos) == 0:
+        return -np.inf
+    k = int(np.floor(fn_target * len(pos)))
+    return float(pos[k]) if k < len(pos) else float(pos[-1])
+
+
+def continuous(ctx, prm, sched, h, R, seed_stream, K, k_dec, E_gs, chunks, net=None,
+               theta=-np.inf, stream=0):
+    """Integrate R slots (R a multiple of len(h)), every slot always busy, for `chunks`
+    chunks of k_dec steps.  With a network, slots at their decision step whose logit
+    is below theta are retired.  Restarted slots take the next pump values of the
+    grid in turn, so the time a retirement saves is spent on fresh runs of every
+    pump, not only of the retired run's own pump.  Returns an Outcome."""
+    torch = _torch()
+    out = Outcome()
+    n_h = len(h)
+    next_h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seeds = seed_stream.take(R)
+    ctx.run(prm, h, seeds, 0, sched, stream)
+    offs = torch.zeros(R, dtype=torch.int64, device="cuda")
+    el = ctx.N * ctx.D * R
+    snap = torch.empty(el, dtype=torch.float64 if prm.prec == chym.PREC_FP64 else torch.float32,
+                       device="cuda")
+    F = torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda")
+    E_dev = torch.empty(R, dtype=torch.float64, device="cuda")
+    for _ in range(chunks):
+        ctx.run(prm, None, None, k_dec // 2, sched, stream, n_runs=R)
+        if net is not None:
+            ctx.copy_state_device(snap.data_ptr(), stream)
+        ctx.run(prm, None, None, k_dec - k_dec // 2, sched, stream, n_runs=R)
+        out.run_steps += R * k_dec
+        k_now = ctx.info()[2]
+        ctx.offsets_device(offs.data_ptr(), stream)
+        local = k_now - offs
+        done = local >= K
+        restart = done.clone()
+        if bool(done.any()):
+            ctx.energy_device(E_dev.data_ptr(), 0, stream)
+            hit = (E_dev - E_gs).abs() <= 1e-9 * max(1.0, abs(E_gs))
+            out.hits += int((hit & done).sum().item())
+            out.completed += int(done.sum().item())
+        if net is not None:
+            at_dec = local == k_dec
+            if bool(at_dec.any()):
+                ctx.features_device(snap.data_ptr(), k_dec / K, F.data_ptr(), stream)
+                z = logits(net, F, stream)
+                retire = at_dec & (z < theta)
+                out.retired += int(retire.sum().item())
+                restart |= retire
+        idx = torch.nonzero(restart).flatten().to(torch.int32)
+        if idx.numel():
+            n = idx.numel()
+            fresh = torch.from_numpy(seed_stream.take(n).view(np.int64)).cuda()
+            pumps = torch.from_numpy(((next_h + np.arange(n)) % n_h).astype(np.int32)).cuda()
+            next_h = (next_h + n) % n_h
+            ctx.reseed_device(idx.data_ptr(), n, fresh.data_ptr(), prm.init_std, pumps.data_ptr(),
+                              stream)
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    out.seconds = time.perf_counter() - t0
+    return out

@@ -134,3 +134,54 @@ def test_adam_steps_follow_reference(torch):
     assert np.max(np.abs(th_gpu - th)) <= 1e-4
     assert M.loss(th, *args) < M.loss(theta.astype(np.float64), *args)
     net.close()
+
+
+def test_learned_early_exit_gains_over_the_plain_method(torch):
+    """SK +-1 N=24, D=3, 16 pumps, K=3000 steps, decision at 10 % (step 300).
+
+    The network is trained on GPU-generated trajectories; its threshold is set for a
+    10 % false-negative rate on a calibration split and judged on a held-out split
+    against the full plain integration of the same seeds.  In continuous operation
+    (every slot always busy, retired slots reseeded) the ground-state hits per
+    integration step must beat the plain method's."""
+    from paper_2308_02329_gb300 import early_exit as EE
+    N, D, K, k_dec, n_h = 24, 3, 3000, 300, 16
+    J = inputs.sk_pm1(N, 77)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=0.5 / ctx.lambda_max(), prec=chym.PREC_BF16X2)
+    sched = chym.Schedule(1, K // 2, K)
+    h = inputs.pump_grid(0.5, n_h)
+    E_gs = ctx.ground_state_exact()[0]
+    assert E_gs == O.ground_state_bruteforce(J)[0]
+    F, y, E = EE.generate(ctx, prm, sched, h, inputs.run_seeds(1, n_h * 1024), K, k_dec, E_gs)
+    Fv, yv, Ev = EE.generate(ctx, prm, sched, h, inputs.run_seeds(2, n_h * 512), K, k_dec, E_gs)
+    net = chym.MLP(seed=4, max_batch=1024)
+    EE.train(net, F, y, epochs=60, batch=512, lr=2e-3)
+    sv = EE.logits(net, Fv).cpu().numpy()
+    yvn = yv.cpu().numpy()
+    perm = np.random.default_rng(0).permutation(len(sv))
+    cal, tst = perm[: len(sv) // 2], perm[len(sv) // 2:]
+    theta = EE.threshold_for_fn(sv[cal], yvn[cal], 0.1)
+    pos = yvn[tst] > 0.5
+    n_pos = int(pos.sum())
+    fn = float(np.mean(sv[tst][pos] < theta))
+    rho = float(np.mean(sv[tst] < theta))
+    assert n_pos >= 20
+    assert fn <= 0.1 + 2.0 * np.sqrt(0.1 * 0.9 / n_pos)          # binomial 95 % bound
+    expected_gain = (1 - fn) / (1 - (1 - k_dec / K) * rho)
+    assert expected_gain > 1.2
+    R = n_h * 128
+    chunks = 80
+    plain = EE.continuous(ctx, prm, sched, h, R, EE.SeedStream(10), K, k_dec, E_gs, chunks)
+    learned = EE.continuous(ctx, prm, sched, h, R, EE.SeedStream(10), K, k_dec, E_gs, chunks,
+                            net, theta)
+    # plain continuous operation reproduces the success probability of the full runs
+    p_full = yvn.mean()
+    p_plain = plain.hits / plain.completed
+    se = np.sqrt(p_full * (1 - p_full) / len(yvn) + p_plain * (1 - p_plain) / plain.completed)
+    assert abs(p_plain - p_full) <= 1.96 * se + 1e-12
+    # runs the network lets through succeed more often than the plain method's
+    assert learned.hits / learned.completed > p_plain
+    assert learned.hits_per_mstep > 1.05 * plain.hits_per_mstep
+    net.close()
+    ctx.close()
