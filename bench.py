@@ -177,6 +177,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def merge_over_ranks(elapsed, hits, dist, device):
+    """Whole-job view of one timed region: the slowest rank's time (max) and the
+    ground-state hits of all ranks (sum).  Each rank integrates its own replica of
+    the workload, so there is no exchange on the data path; this is the only
+    collective, once per timed region."""
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    h = torch.tensor([float(hits)], dtype=torch.float64, device=device)
+    dist.all_reduce(h, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(h.item())
+
+
 def oracle_jobs(w):
     """(J, D, oracle params, oracle schedule) of every (graph, D) of a workload."""
     import oracle.oracle as O
@@ -365,12 +378,7 @@ def main():
         torch.cuda.synchronize()
         el = t0.elapsed_time(t1) / 1e3
         if world > 1:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-            ht = torch.tensor([hits], device=dev, dtype=torch.float64)
-            dist.all_reduce(ht)
-            hits = int(ht.item())
+            el, hits = merge_over_ranks(el, hits, dist, dev)
         return el, hits
 
     # warm-up; the references of non-exact instances also take the best energy found
@@ -454,9 +462,7 @@ def main():
         torch.cuda.synchronize()
         el2 = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([el2], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el2 = float(t.item())
+            el2, _ = merge_over_ranks(el2, 0, dist, dev)
         h2d = sum(w.n_h * 8 + w.runs * 8 for _ in jobs)
         d2h = sum(w.runs * 8 + 64 + w.n_h * 8 for _ in jobs)
         e2e = {"value": work_step * args.steps * world / el2, "unit": UNIT,
