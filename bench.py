@@ -7,10 +7,15 @@ values x 128 replicas, 20000 Euler-Maruyama steps (dt = 0.01; D >= 3 anneal
 linearly over the second half), then the Ising readout, energies and
 ground-state statistics.  Other workloads (--workload): "sk1000" (SK +-1 and
 Gaussian N=1000, D=4, 16384 runs, 50000 steps) and "sk800" (SK +-1 N=800, D=4,
-65536 runs, 50000 steps), which run on the large-N tensor-core path.
+65536 runs, 50000 steps), which run on the large-N tensor-core path, and "uneven"
+(512 SK +-1 instances, N uniform in [50, 2000], D in {2,3,4,8}, 64 runs each over
+16 pumps, 30000 steps) as one batch whose planner costs are tuned on the device.
 
 Metric: hyperspin-steps/s (N * D * runs * steps per second) and ground-state
-hits per second.
+hits per second.  Beside the mixed-precision form the line carries the plain
+FP32 form of the same workload and, for the default workload, the mixed form
+with the learned early exit in continuous operation (finished and retired runs
+reseeded), each with its ground-state hits per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n100|sk1000|sk800]
   python bench.py --impl reference ...   # the FP64 CPU checker on the host cores
@@ -51,6 +56,7 @@ class Workload:
     reps: int
     steps: int
     compare_plain: bool = True
+    learned: bool = False
     notes: dict = field(default_factory=dict)
 
     @property
@@ -61,7 +67,8 @@ class Workload:
 WORKLOADS = {
     "n100": Workload("n100", "moebius N=100 + SK+-1 N=100, D in {2,3,4}, 4096 runs/graph "
                      "(32 h x 128 replicas), 20000 steps dt=0.01",
-                     [("moebius", "moebius", 100), ("sk", "sk", 100)], (2, 3, 4), 32, 128, 20000),
+                     [("moebius", "moebius", 100), ("sk", "sk", 100)], (2, 3, 4), 32, 128, 20000,
+                     learned=True),
     "sk1000": Workload("sk1000", "SK+-1 and Gaussian N(0,1/N) N=1000, D=4, 16384 runs "
                        "(32 h x 512 replicas), 50000 steps dt=0.01",
                        [("sk", "sk", 1000), ("gauss", "gauss", 1000)], (4,), 32, 512, 50000,
@@ -69,15 +76,29 @@ WORKLOADS = {
     "sk800": Workload("sk800", "SK+-1 N=800, D=4, 65536 runs (32 h x 2048 replicas), "
                       "50000 steps dt=0.01",
                       [("sk", "sk", 800)], (4,), 32, 2048, 50000, compare_plain=False),
+    "uneven": Workload("uneven", "512 SK+-1 instances, N uniform in [50, 2000], D uniform in "
+                       "{2,3,4,8}, 64 runs each (16 h x 4 replicas), 30000 steps dt=0.01, "
+                       "one tuned batch", [], (2, 3, 4, 8), 16, 4, 30000, compare_plain=False),
 }
+UNEVEN_INSTANCES = 512
 
 
-def build_graph(kind, N, rank):
+def workload_specs(w, rank):
+    """(name, graph kind, N, D, instance seed or None) of every context of a workload."""
+    if w.key == "uneven":
+        from paper_2308_02329_gb300 import inputs
+        comp = inputs.uneven_instances(UNEVEN_INSTANCES, INSTANCE_SEED + 4)
+        return [(f"sk{N}_{i}", "sk", N, D, seed + 1000003 * rank)
+                for i, (N, D, seed) in enumerate(comp)]
+    return [(name, kind, N, D, None) for name, kind, N in w.graphs for D in w.D]
+
+
+def build_graph(kind, N, rank, seed=None):
     from paper_2308_02329_gb300 import inputs
     if kind == "moebius":
         return inputs.mobius_ladder(N)
     if kind == "sk":
-        return inputs.sk_pm1(N, INSTANCE_SEED + 1 + 1000 * rank)
+        return inputs.sk_pm1(N, seed if seed is not None else INSTANCE_SEED + 1 + 1000 * rank)
     return inputs.gaussian(N, INSTANCE_SEED + 2 + 1000 * rank)
 
 
@@ -90,8 +111,9 @@ def mode_for(D):
 
 
 def workload_config(w, prec_name, sim_steps):
-    return {"workload": w.title, "key": w.key,
-            "graphs": [f"{n}_{N}" for n, _, N in w.graphs], "D": list(w.D),
+    graphs = ([f"{n}_{N}" for n, _, N in w.graphs] if w.graphs else
+              [f"{UNEVEN_INSTANCES} SK+-1 instances, N in [50, 2000]"])
+    return {"workload": w.title, "key": w.key, "graphs": graphs, "D": list(w.D),
             "runs_per_graph": w.runs, "n_h": w.n_h, "replicas": w.reps, "steps": sim_steps,
             "precision": prec_name, "l2": "flushed between steps (256 MiB write)"}
 
@@ -191,17 +213,23 @@ def merge_over_ranks(elapsed, hits, dist, device):
 
 
 def oracle_jobs(w):
-    """(J, D, oracle params, oracle schedule) of every (graph, D) of a workload."""
+    """(J, D, oracle params, oracle schedule) of every (graph, D) of a workload; for the
+    uneven workload, of every 32nd instance (a bounded sample)."""
     import oracle.oracle as O
     jobs = []
-    for name, kind, N in w.graphs:
-        J = build_graph(kind, N, 0)
-        lam = float(np.linalg.eigvalsh(J)[-1])
-        for D in w.D:
-            kappa, skind = mode_for(D)
-            prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
-                           eps=EPS_HAT / lam)
-            jobs.append((J, D, prm, O.Schedule(skind, w.steps // 2, w.steps)))
+    specs = workload_specs(w, 0)
+    if w.key == "uneven":
+        specs = specs[::32]
+    cache = {}
+    for name, kind, N, D, seed in specs:
+        if (kind, N, seed) not in cache:
+            J = build_graph(kind, N, 0, seed)
+            cache[(kind, N, seed)] = (J, float(np.linalg.eigvalsh(J)[-1]))
+        J, lam = cache[(kind, N, seed)]
+        kappa, skind = mode_for(D)
+        prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
+                       eps=EPS_HAT / lam)
+        jobs.append((J, D, prm, O.Schedule(skind, w.steps // 2, w.steps)))
     return jobs
 
 
@@ -231,7 +259,7 @@ def cpu_baseline_sample(w, target_s=10.0):
     el = time_oracle(jobs, runs, steps, threads)
     work = sum(J.shape[0] * D * runs * steps for J, D, _, _ in jobs)
     return {"value": work / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"every (graph, D) of the workload, {runs} runs x {steps} of "
+            "sample": f"{len(jobs)} (graph, D) contexts of the workload, {runs} runs x {steps} of "
                       f"{w.steps} steps each, FP64, OpenMP over runs; {el:.1f} s"}
 
 
@@ -250,7 +278,7 @@ def run_reference(args, w, rank, world):
     el = sum(time_oracle(jobs, runs, steps, threads) for _ in range(args.steps))
     work = sum(J.shape[0] * D * runs * steps for J, D, _, _ in jobs)
     value = work * args.steps / el
-    sample = (f"per step: every (graph, D) of the workload, {runs} runs x {steps} of {w.steps} "
+    sample = (f"per step: {len(jobs)} (graph, D) contexts of the workload, {runs} runs x {steps} of {w.steps} "
               f"steps each, FP64, OpenMP over runs")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -265,6 +293,75 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
+    """Mixed precision + learned early exit on the same contexts.
+
+    Setup (untimed): every context generates labelled trajectories with its own fresh
+    seeds (features at 10 % of the schedule, outcome at the end), one network is
+    trained on all of them on the GPU, and its retire threshold is set for a 10 %
+    false-negative rate on half of a held-out set; the other half measures it.
+    Timed: continuous operation (every slot always busy, finished and retired slots
+    reseeded) of all contexts as one batch for `chunks` chunks of 10 % of the
+    schedule, with and without the network.  Returns the leg's JSON object."""
+    import torch
+    from paper_2308_02329_gb300 import chym
+    from paper_2308_02329_gb300 import early_exit as EE
+    from paper_2308_02329_gb300 import inputs
+    K, k_dec = sim_steps, sim_steps // 10
+    sp = stream.cuda_stream
+    Fs, ys, Fv, yv = [], [], [], []
+    t_setup = time.perf_counter()
+    for i, j in enumerate(jobs):
+        F, y, _ = EE.generate(j["ctx"], j["prm"], j["sched"], j["h"],
+                              inputs.run_seeds(0x5EED0000 + i, w.runs), K, k_dec, gs[j["name"]], sp)
+        Fs.append(F)
+        ys.append(y)
+        F, y, _ = EE.generate(j["ctx"], j["prm"], j["sched"], j["h"],
+                              inputs.run_seeds(0x7A1D0000 + i, w.runs // 2), K, k_dec, gs[j["name"]],
+                              sp)
+        Fv.append(F)
+        yv.append(y)
+    F, y = torch.cat(Fs), torch.cat(ys)
+    net = chym.MLP(seed=4, max_batch=1024)
+    loss = EE.train(net, F, y, epochs=30, batch=512, lr=2e-3, stream=sp)
+    Fv, yv = torch.cat(Fv), torch.cat(yv)
+    sv = EE.logits(net, Fv, sp).cpu().numpy()
+    yvn = yv.cpu().numpy()
+    perm = np.random.default_rng(0).permutation(len(sv))
+    cal, tst = perm[: len(sv) // 2], perm[len(sv) // 2:]
+    theta = EE.threshold_for_fn(sv[cal], yvn[cal], 0.1)
+    pos = yvn[tst] > 0.5
+    fn = float(np.mean(sv[tst][pos] < theta)) if pos.any() else None
+    setup_s = time.perf_counter() - t_setup
+
+    def run(with_net, key):
+        streams = [EE.SeedStream(key + i) for i in range(len(jobs))]
+        return EE.continuous_many([j["ctx"] for j in jobs], [j["prm"] for j in jobs],
+                                  [j["sched"] for j in jobs], [j["h"] for j in jobs],
+                                  [w.runs] * len(jobs), streams, K, k_dec,
+                                  [gs[j["name"]] for j in jobs], chunks,
+                                  net if with_net else None, theta, sp, batch=batch)
+    mixed = run(False, 0xC0A7)
+    learned = run(True, 0xC0A7)
+    net.close()
+    out = {"gs_hits_per_s": learned.hits_per_second,
+           "mixed_continuous_gs_hits_per_s": mixed.hits_per_second,
+           "gain_vs_mixed": learned.hits_per_second / mixed.hits_per_second
+           if mixed.hits_per_second > 0 else None,
+           "hits_per_mstep": {"learned": learned.hits_per_mstep, "mixed": mixed.hits_per_mstep},
+           "completed": {"learned": learned.completed, "mixed": mixed.completed},
+           "retired": learned.retired, "seconds": {"learned": learned.seconds,
+                                                   "mixed": mixed.seconds},
+           "p_success_completed": {"learned": learned.hits / max(learned.completed, 1),
+                                   "mixed": mixed.hits / max(mixed.completed, 1)},
+           "fn_rate_heldout": fn, "fn_target": 0.1, "positives_heldout": int(pos.sum()),
+           "train_rows": int(F.shape[0]), "train_loss": loss, "setup_s": setup_s,
+           "window": f"{chunks} chunks of {k_dec} steps (decision at 10 % of {K})"}
+    if plain and plain["gs_hits_per_s"] > 0:
+        out["ratio_vs_plain_fp32"] = learned.hits_per_second / plain["gs_hits_per_s"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -276,6 +373,9 @@ def main():
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-chunks", type=int, default=40,
+                    help="chunks of 10 %% of the schedule in the learned leg's timed window")
     ap.add_argument("--sim-steps", type=int, default=0,
                     help="integration steps per run (default: the workload's); for profiling")
     ap.add_argument("--replicas", type=int, default=0,
@@ -306,34 +406,56 @@ def main():
 
     # ---------------- setup (untimed): instances, references, device inputs ----------
     jobs, gs = [], {}
-    for gi, (name, kind, N) in enumerate(w.graphs):
-        J = build_graph(kind, N, rank)
+    graphs = {}
+    for gi, (name, kind, N, D, seed) in enumerate(workload_specs(w, rank)):
+        if name not in graphs:
+            J = build_graph(kind, N, rank, seed)
+            graphs[name] = J
+            jkind = chym.J_REAL if kind == "gauss" else chym.J_PM1
+            if kind == "moebius":
+                gs[name] = chym.ground_state_mobius(N)
+            elif w.key == "uneven":
+                gs[name] = float("inf")    # best energy of the warm-up runs (below)
+            else:
+                c1 = chym.Context(J, 1, jkind)
+                restarts, sweeps = (64, 2000) if N <= 200 else (4, 400)
+                gs[name] = c1.ground_state_search(restarts=restarts, sweeps=sweeps, seed=11)[0]
+                c1.close()
+        J = graphs[name]
         jkind = chym.J_REAL if kind == "gauss" else chym.J_PM1
-        for D in w.D:
-            ctx = chym.Context(J, D, jkind)
-            lam = ctx.lambda_max()
-            kappa, skind = mode_for(D)
-            prm = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
-                              eps=EPS_HAT / lam, prec=prec)
-            sched = chym.Schedule(skind, sim_steps // 2 if skind else 0, sim_steps)
-            h = inputs.pump_grid(1.0 - EPS_HAT, w.n_h)
-            seeds = inputs.run_seeds(INSTANCE_SEED + 7919 * rank + 97 * gi + D, w.runs)
-            jobs.append(dict(name=name, N=N, J=J, D=D, ctx=ctx, prm=prm, sched=sched, h=h,
-                             seeds=seeds, d_h=torch.from_numpy(h).to(dev),
-                             d_seeds=torch.from_numpy(seeds.view(np.int64)).to(dev),
-                             d_E=torch.empty(w.runs, dtype=torch.float64, device=dev),
-                             nnz=int((J != 0).sum(1).mean())))
-        if kind == "moebius":
-            gs[name] = chym.ground_state_mobius(N)
-        else:
-            c1 = chym.Context(J, 1, jkind)
-            restarts, sweeps = (64, 2000) if N <= 200 else (4, 400)
-            gs[name] = c1.ground_state_search(restarts=restarts, sweeps=sweeps, seed=11)[0]
-            c1.close()
+        ctx = chym.Context(J, D, jkind)
+        kappa, skind = mode_for(D)
+        h = inputs.pump_grid(1.0 - EPS_HAT, w.n_h)
+        sd = INSTANCE_SEED + 7919 * rank + 97 * gi + D if seed is None else seed
+        seeds = inputs.run_seeds(sd, w.runs)
+        jobs.append(dict(name=name, N=N, D=D, ctx=ctx, kappa=kappa, skind=skind, h=h,
+                         seeds=seeds, d_h=torch.from_numpy(h).to(dev),
+                         d_seeds=torch.from_numpy(seeds.view(np.int64)).to(dev),
+                         d_E=torch.empty(w.runs, dtype=torch.float64, device=dev),
+                         nnz=int((J != 0).sum(1).mean())))
+        if w.key == "uneven":
+            del graphs[name]     # the context holds its own copy of J
+    # lambda_max of every context (host Lanczos; ctypes releases the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as pool:
+        lams = list(pool.map(lambda j: j["ctx"].lambda_max(), jobs))
+    for j, lam in zip(jobs, lams):
+        j["prm"] = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=j["kappa"],
+                               eps=EPS_HAT / lam, prec=prec)
+        j["sched"] = chym.Schedule(j["skind"], sim_steps // 2 if j["skind"] else 0, sim_steps)
+    graphs.clear()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     streams = [torch.cuda.Stream(dev) for _ in jobs]
     batch = chym.Batch([j["ctx"] for j in jobs])
     spans = []
+    tuning = None
+    if w.key == "uneven":
+        # the planner's cost model, measured for this batch (setup, untimed)
+        for j in jobs:
+            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), w.n_h, j["d_seeds"].data_ptr(),
+                                w.runs, 0, j["sched"], stream.cuda_stream)
+        tuning = batch.tune([j["prm"] for j in jobs], [j["sched"] for j in jobs],
+                            probe_steps=32, stream=stream.cuda_stream)
 
     def one_step(record=False):
         """init every (graph, D), integrate all of them together as one batch (persistent
@@ -468,17 +590,26 @@ def main():
         e2e = {"value": work_step * args.steps * world / el2, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---------------- mixed + learned early exit (continuous operation) ----------------
+    learned = None
+    if w.learned and not args.no_learned and prec == chym.PREC_BF16X2 and world == 1:
+        learned = learned_leg(jobs, w, sim_steps, gs, batch, stream, args.learned_chunks, plain)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline_sample(w)
-        # launches of our kernels per bench step: init, energy and statistics per
-        # (graph, D); one persistent launch per dimension for the small-N contexts; the
-        # large-N path adds 3 layout kernels and one GEMM launch per integration step
-        small = [j for j in jobs if j["N"] <= 128 and prec == chym.PREC_BF16X2]
-        large = [j for j in jobs if j not in small]
-        per_step = 3 * len(jobs) + len({j["D"] for j in small}) + sum(
-            (4 + sim_steps) if prec == chym.PREC_BF16X2 else 1 for j in large)
+        # launches of our kernels per bench step: pump indices, init, energy and
+        # statistics per context; one persistent launch per dimension for the small-N
+        # contexts; the large-N path adds 3 layout kernels per context, one grouped GEMM
+        # launch per dimension and integration step, and one step-counter kernel per
+        # 16-step graph; FP32/FP64 contexts take one persistent SIMT launch each
+        bf16 = prec == chym.PREC_BF16X2
+        small = [j for j in jobs if j["N"] <= 128 and bf16]
+        large = [j for j in jobs if j["N"] > 128 and bf16]
+        per_step = 4 * len(jobs) + len({j["D"] for j in small}) + 3 * len(large) + (
+            sim_steps * len({j["D"] for j in large}) + sim_steps // 16 if large else 0) + (
+            0 if bf16 else len(jobs))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -492,6 +623,11 @@ def main():
                 "gs_hits_ratio_vs_plain": (hits_total / elapsed) / plain["gs_hits_per_s"]
                 if plain and plain["gs_hits_per_s"] > 0 else None,
                 "gpu_launches": args.steps * per_step}
+        if tuning is not None:
+            line["tuning"] = tuning
+        if learned is not None:
+            line["learned"] = learned
+            line["gs_hits_ratio_learned_vs_plain"] = learned.get("ratio_vs_plain_fp32")
         print(json.dumps(line), flush=True)
     batch.close()
     for j in jobs:

@@ -234,6 +234,29 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
  * bounded device-side wait of a batched launch gave up. */
 CHYM_API chym_status chym_batch_status(chym_batch* b);
 
+/* Autotuner of the batch planner.  The planner splits the SMs between the
+ * small-N dimensions and the large-N launches in proportion to their estimated
+ * work, from a cost model in SM-microseconds: per dimension D, one chunk of runs
+ * (8 runs for D <= 4, 4 above) advanced one step on the small-N path; and one
+ * unit of the large-N path (a 128-row output tile x one 64-wide K chunk) advanced
+ * one step.  chym_batch_tune measures these costs on the current device for the
+ * batch's own contexts: each group (the small-N contexts of one D, and all
+ * large-N contexts) is integrated alone on the whole GPU for probe_steps steps,
+ * once to warm up and once timed with CUDA events.  Every context's state, step
+ * and energies are restored afterwards, so tuning does not change any result.
+ * Synchronous; needs the contexts' states (ESTATE otherwise); probe_steps >= 1. */
+CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
+                                     const chym_schedule* schedules, int64_t probe_steps,
+                                     void* cuda_stream);
+/* The cost model: chunk_costs[D-1] for D = 1..8 and k2_cost (SM-microseconds),
+ * tuned = 1 once measured or set.  Outputs may be NULL.  With set, a caller
+ * restores costs it cached from an earlier tuning (positive and finite values;
+ * NULL keeps the current ones). */
+CHYM_API chym_status chym_batch_get_tuning(chym_batch* b, double* chunk_costs, double* k2_cost,
+                                           int* tuned);
+CHYM_API chym_status chym_batch_set_tuning(chym_batch* b, const double* chunk_costs,
+                                           const double* k2_cost);
+
 CHYM_API chym_status chym_batch_destroy(chym_batch* b);
 
 /* ---- Learned early exit (no counterpart in the paper's method; a layer on top of

@@ -26,6 +26,7 @@ EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", 
            "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
            "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
            "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
+           "chym_batch_tune", "chym_batch_get_tuning", "chym_batch_set_tuning",
            "chym_reseed_device", "chym_get_offsets_device", "chym_copy_state_device",
            "chym_features_device", "chym_mlp_create", "chym_mlp_destroy", "chym_mlp_set_params",
            "chym_mlp_get_params", "chym_mlp_forward_device", "chym_mlp_grad_device",
@@ -127,6 +128,9 @@ def lib():
         L.chym_batch_run.argtypes = [vp, ctypes.POINTER(CParams), ctypes.POINTER(CSchedule), i64, vp]
         L.chym_batch_status.argtypes = [vp]
         L.chym_batch_destroy.argtypes = [vp]
+        L.chym_batch_tune.argtypes = [vp, ctypes.POINTER(CParams), ctypes.POINTER(CSchedule), i64, vp]
+        L.chym_batch_get_tuning.argtypes = [vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+        L.chym_batch_set_tuning.argtypes = [vp, vp, vp]
         L.chym_stats_noalloc.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(CStats), vp, vp,
                                          i32, vp]
         for name in EXPORTS:
@@ -341,6 +345,51 @@ class Batch:
 
     def status(self):
         _check(lib().chym_batch_status(self._h))
+
+    def tuning(self):
+        """The planner's cost model: {"chunk": [D=1..8], "k2": float, "tuned": bool}."""
+        c = (ctypes.c_double * 8)()
+        k2 = ctypes.c_double()
+        t = ctypes.c_int32()
+        _check(lib().chym_batch_get_tuning(self._h, c, ctypes.byref(k2), ctypes.byref(t)))
+        return {"chunk": list(c), "k2": k2.value, "tuned": bool(t.value)}
+
+    def set_tuning(self, tuning):
+        c = (ctypes.c_double * 8)(*tuning["chunk"])
+        k2 = ctypes.c_double(tuning["k2"])
+        _check(lib().chym_batch_set_tuning(self._h, c, ctypes.byref(k2)))
+
+    def signature(self, device_key=""):
+        """Key of the batch's composition for a tuning cache."""
+        import hashlib
+        parts = sorted((c.N, c.D, c.kind, c.info()[0]) for c in self.contexts)
+        return hashlib.sha1(repr((device_key, parts)).encode()).hexdigest()[:16]
+
+    def tune(self, params, schedules, probe_steps=64, stream=0, cache_path=None, device_key=""):
+        """Measure the cost model (chym_batch_tune).  With cache_path, a JSON file of
+        earlier tunings keyed by device_key and the batch's composition: a hit sets
+        the cached costs without measuring, a miss measures and adds the entry."""
+        import json
+        import os
+        key = self.signature(device_key)
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+            if key in cache:
+                self.set_tuning(cache[key])
+                return self.tuning()
+        P = (CParams * len(self.contexts))(*[p.c() for p in params])
+        S = (CSchedule * len(self.contexts))(*[s.c() for s in schedules])
+        _check(lib().chym_batch_tune(self._h, P, S, int(probe_steps), ctypes.c_void_p(stream)))
+        out = self.tuning()
+        if cache_path:
+            cache[key] = {"chunk": out["chunk"], "k2": out["k2"]}
+            tmp = cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache_path)
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -33,8 +33,13 @@ struct chym_batch {
   unsigned* d_status = nullptr;
   int sms = 0;
   chym::K2Runner k2;
-  // per-dimension relative cost of one chunk-step (tuned by chym_batch_tune)
-  double chunk_cost[9] = {0, 1.0, 0.58, 0.83, 0.92, 1.15, 1.3, 1.45, 1.6};
+  // Cost model of the planner, in SM-microseconds: one 8- or 4-run chunk advanced
+  // one step on the small-N path, per dimension D; and one (128-row tile x K chunk
+  // of 64) advanced one step on the large-N path.  The defaults were measured on a
+  // GB300; chym_batch_tune re-measures them for the batch's own contexts.
+  double chunk_cost[9] = {0, 1.10, 0.64, 0.91, 1.01, 1.27, 1.43, 1.60, 1.76};
+  double k2_cost = 1.05;
+  bool tuned = false;
 };
 
 namespace chym {
@@ -166,6 +171,9 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
       if (e != cudaSuccess) return cuda_fail(e, "J operand image");
     }
   }
+  // work in SM-microseconds per step: each small-N dimension and the large-N group.
+  // The SMs are split in proportion, so that all parts finish together; the
+  // large-N launches take the SMs that the persistent small-N CTAs leave free.
   double cost[9] = {0};
   double total = 0.0;
   for (int D = 1; D <= 8; ++D) {
@@ -175,6 +183,16 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     }
     total += cost[D];
   }
+  double small_total = total;
+  for (int i = 0; i < n; ++i) {
+    const chym_ctx* c = b->ctxs[i];
+    if (params[i].prec == CHYM_PREC_BF16X2 && c->N > 128)
+      total += b->k2_cost * (double)k2_work_units(c->N, c->D, c->n_runs);
+  }
+  // SMs for the small-N dimensions (all of them when there is no large-N work)
+  const int sms_small = small_total > 0.0
+                            ? std::min(b->sms, std::max(1, (int)llround(b->sms * small_total / total)))
+                            : 0;
   // plan: descriptors of all small-N contexts, then per dimension its items and CTA ranges
   std::vector<unsigned char> blob;
   const size_t db = tc_desc_bytes();
@@ -192,12 +210,13 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     size_t items_off, cta_off;
   };
   std::vector<DimLaunch> dl;
-  int sms_left = b->sms;
   int dims_left = 0;
   for (int D = 1; D <= 8; ++D) dims_left += by_dim[D].empty() ? 0 : 1;
+  int sms_left = std::max(sms_small, dims_left);
   for (int D = 1; D <= 8; ++D) {
     if (by_dim[D].empty()) continue;
-    int P = std::max(1, (int)llround(b->sms * cost[D] / total));
+    int P = std::max(1, (int)llround(sms_left * cost[D] / small_total));
+    small_total -= cost[D];
     P = std::min(P, sms_left - (dims_left - 1));
     P = std::max(P, 1);
     sms_left -= P;
@@ -303,6 +322,148 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   }
   for (int i = 0; i < n; ++i)
     if (used[i]) CHYM_CUDA_TRY(cudaStreamWaitEvent(main, b->joins[i], 0));
+  return CHYM_OK;
+}
+
+// Autotuner: measure the planner's cost model on this device for the batch's own
+// contexts.  Each group (the small-N contexts of one dimension D; all large-N
+// contexts) is integrated alone on the whole GPU for probe_steps steps, once to
+// warm up (first launches, graph capture) and once timed with CUDA events; the
+// states, steps and energies of the contexts are saved before and restored after.
+CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
+                                     const chym_schedule* schedules, int64_t probe_steps,
+                                     void* cuda_stream) {
+  if (!b || !params || !schedules) return fail(CHYM_EINVAL, "NULL argument");
+  if (probe_steps < 1) return fail(CHYM_EINVAL, "probe_steps must be >= 1");
+  const int n = (int)b->ctxs.size();
+  for (int i = 0; i < n; ++i)
+    if (b->ctxs[i]->prec < 0) return fail(CHYM_ESTATE, "every context needs a state (chym_run with seeds first)");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // groups: 1..8 small-N dimensions, 0 the large-N contexts
+  std::vector<int> groups[9];
+  for (int i = 0; i < n; ++i) {
+    const chym_ctx* c = b->ctxs[i];
+    if (params[i].prec != CHYM_PREC_BF16X2) continue;
+    groups[c->N <= 128 ? c->D : 0].push_back(i);
+  }
+  // save the states of every context that takes part
+  struct Saved {
+    void* d = nullptr;
+    size_t bytes = 0;
+    int64_t k = 0;
+    bool have_energy = false;
+  };
+  std::vector<Saved> saved(n);
+  auto release = [&]() {
+    for (auto& sv : saved)
+      if (sv.d) cudaFree(sv.d);
+  };
+  for (int g = 0; g <= 8; ++g)
+    for (int i : groups[g]) {
+      chym_ctx* c = b->ctxs[i];
+      Saved& sv = saved[i];
+      sv.bytes = (size_t)c->n_runs * c->N * c->D * (c->prec == CHYM_PREC_FP64 ? 8 : 4);
+      sv.k = c->k;
+      sv.have_energy = c->have_energy;
+      cudaError_t e = cudaMalloc(&sv.d, sv.bytes);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(sv.d, c->d_X, sv.bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "chym_batch_tune: state snapshot");
+      }
+    }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  chym_status status = CHYM_OK;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) status = cuda_fail(e, "chym_batch_tune: events");
+  double new_chunk[9];
+  for (int D = 0; D <= 8; ++D) new_chunk[D] = b->chunk_cost[D];
+  double new_k2 = b->k2_cost;
+  for (int g = 0; g <= 8 && status == CHYM_OK; ++g) {
+    if (groups[g].empty()) continue;
+    std::vector<chym_ctx*> cs;
+    std::vector<chym_params> ps;
+    std::vector<chym_schedule> ss;
+    for (int i : groups[g]) {
+      cs.push_back(b->ctxs[i]);
+      ps.push_back(params[i]);
+      ss.push_back(schedules[i]);
+    }
+    chym_batch* sub = nullptr;
+    status = chym_batch_create(cs.data(), (int)cs.size(), &sub);
+    if (status != CHYM_OK) break;
+    float ms = 0.f;
+    status = chym_batch_run(sub, ps.data(), ss.data(), probe_steps, st);
+    if (status == CHYM_OK) {
+      e = cudaEventRecord(t0, st);
+      if (e == cudaSuccess) status = chym_batch_run(sub, ps.data(), ss.data(), probe_steps, st);
+      if (e == cudaSuccess && status == CHYM_OK) e = cudaEventRecord(t1, st);
+      if (e == cudaSuccess && status == CHYM_OK) e = cudaEventSynchronize(t1);
+      if (e == cudaSuccess && status == CHYM_OK) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e != cudaSuccess && status == CHYM_OK) status = cuda_fail(e, "chym_batch_tune: timing");
+    }
+    if (status == CHYM_OK) status = chym_batch_status(sub);
+    chym_batch_destroy(sub);
+    if (status != CHYM_OK) break;
+    const double us = 1e3 * (double)ms;
+    if (g > 0) {
+      long long C = 0;
+      for (chym_ctx* c : cs) C += (c->n_runs + tc_chunk_runs(g) - 1) / tc_chunk_runs(g);
+      const long long P = std::min<long long>(b->sms, C);
+      const long long per_cta = (C + P - 1) / P;
+      new_chunk[g] = us / ((double)per_cta * (double)probe_steps);
+    } else {
+      long long U = 0;
+      for (chym_ctx* c : cs) U += k2_work_units(c->N, c->D, c->n_runs);
+      new_k2 = us * (double)b->sms / ((double)U * (double)probe_steps);
+    }
+  }
+  // restore the states
+  for (int g = 0; g <= 8; ++g)
+    for (int i : groups[g]) {
+      chym_ctx* c = b->ctxs[i];
+      const Saved& sv = saved[i];
+      if (!sv.d) continue;
+      e = cudaMemcpyAsync(c->d_X, sv.d, sv.bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess && status == CHYM_OK) status = cuda_fail(e, "chym_batch_tune: state restore");
+      c->k = sv.k;
+      c->have_energy = sv.have_energy;
+    }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess && status == CHYM_OK) status = cuda_fail(e, "chym_batch_tune");
+  release();
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (status != CHYM_OK) return status;
+  for (int D = 0; D <= 8; ++D) b->chunk_cost[D] = new_chunk[D];
+  b->k2_cost = new_k2;
+  b->tuned = true;
+  return CHYM_OK;
+}
+
+CHYM_API chym_status chym_batch_get_tuning(chym_batch* b, double* chunk_costs, double* k2_cost,
+                                           int* tuned) {
+  if (!b) return fail(CHYM_EINVAL, "NULL batch");
+  if (chunk_costs)
+    for (int D = 0; D < 8; ++D) chunk_costs[D] = b->chunk_cost[D + 1];
+  if (k2_cost) *k2_cost = b->k2_cost;
+  if (tuned) *tuned = b->tuned ? 1 : 0;
+  return CHYM_OK;
+}
+
+CHYM_API chym_status chym_batch_set_tuning(chym_batch* b, const double* chunk_costs, const double* k2_cost) {
+  if (!b) return fail(CHYM_EINVAL, "NULL batch");
+  if (chunk_costs)
+    for (int D = 0; D < 8; ++D)
+      if (!(chunk_costs[D] > 0.0) || !isfinite(chunk_costs[D]))
+        return fail(CHYM_EINVAL, "costs must be positive and finite");
+  if (k2_cost && (!(*k2_cost > 0.0) || !isfinite(*k2_cost)))
+    return fail(CHYM_EINVAL, "costs must be positive and finite");
+  if (chunk_costs)
+    for (int D = 0; D < 8; ++D) b->chunk_cost[D + 1] = chunk_costs[D];
+  if (k2_cost) b->k2_cost = *k2_cost;
+  if (chunk_costs || k2_cost) b->tuned = true;
   return CHYM_OK;
 }
 

@@ -181,6 +181,8 @@ cudaError_t launch_step_k2(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 // large-N path over several contexts (chym_k2.cu)
 cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void* desc_out);
 size_t k2_desc_bytes();
+// tiles x K chunks of one step of a large-N context (the planner's work unit)
+long long k2_work_units(int N, int D, int n_runs);
 cudaError_t k2_finish(chym_ctx* c, const void* desc, cudaStream_t st);
 cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
                          const std::vector<int>& dims, int64_t steps, unsigned* status,

@@ -558,6 +558,15 @@ cudaError_t k2_launch(int D, const K2Launch& L, int n_tiles, int terms_max, cuda
 
 }  // namespace
 
+long long k2_work_units(int N, int D, int n_runs) {
+  if (D < 1 || D > 8) return 0;
+  static const int cols[9] = {0, k2_cols(1), k2_cols(2), k2_cols(3), k2_cols(4),
+                              k2_cols(5), k2_cols(6), k2_cols(7), k2_cols(8)};
+  const long long MT = (N + 127) / 128, KC = 2 * MT;
+  const long long CT = ((long long)n_runs * D + cols[D] - 1) / cols[D];
+  return MT * CT * KC;
+}
+
 // A-operand blocks of J (and of its BF16 residual for real couplings).
 cudaError_t prepare_k2_operand(chym_ctx* c) {
   if (c->d_Ak2) return cudaSuccess;

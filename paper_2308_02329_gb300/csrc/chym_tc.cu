@@ -584,8 +584,10 @@ template <int D>
 cudaError_t launch_tc_plan(const TcLaunch& L, int n_cta, cudaStream_t st) {
   using Cfg = TcCfg<D>;
   const size_t b_bytes = (size_t)L.kp_max * Cfg::CG * 2u;
-  // at least 116 KB so that one CTA (which owns all 512 TMEM columns) fits per SM
-  const size_t smem = std::max<size_t>(L.a_region + (size_t)Cfg::G * 2 * b_bytes, 116 * 1024);
+  // at least 128 KB: one CTA owns all 512 TMEM columns of its SM, so neither a
+  // second CTA of this kernel nor a large-N step CTA (>= 104 KB) may be placed
+  // beside it (it would wait in tcgen05.alloc until this CTA exits)
+  const size_t smem = std::max<size_t>(L.a_region + (size_t)Cfg::G * 2 * b_bytes, 128 * 1024);
   auto kern = step_tc_kernel<D>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -127,53 +127,74 @@ def continuous(ctx, prm, sched, h, R, seed_stream, K, k_dec, E_gs, chunks, net=N
     is below theta are retired.  Restarted slots take the next pump values of the
     grid in turn, so the time a retirement saves is spent on fresh runs of every
     pump, not only of the retired run's own pump.  Returns an Outcome."""
+    return continuous_many([ctx], [prm], [sched], [h], [R], [seed_stream], K, k_dec, [E_gs],
+                           chunks, net, theta, stream)
+
+
+def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, chunks,
+                    net=None, theta=-np.inf, stream=0, batch=None):
+    """`continuous` over several contexts at once (one network and threshold for all;
+    the features carry N, D and h).  With `batch` (a chym.Batch over ctxs) every chunk
+    of steps is one batched integration of all contexts."""
     torch = _torch()
     out = Outcome()
-    n_h = len(h)
-    next_h = 0
+    n = len(ctxs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    seeds = seed_stream.take(R)
-    ctx.run(prm, h, seeds, 0, sched, stream)
-    offs = torch.zeros(R, dtype=torch.int64, device="cuda")
-    el = ctx.N * ctx.D * R
-    snap = torch.empty(el, dtype=torch.float64 if prm.prec == chym.PREC_FP64 else torch.float32,
-                       device="cuda")
-    F = torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda")
-    E_dev = torch.empty(R, dtype=torch.float64, device="cuda")
+    per = []
+    for ctx, prm, sched, h, R, ss in zip(ctxs, prms, scheds, hs, Rs, seed_streams):
+        ctx.run(prm, h, ss.take(R), 0, sched, stream)
+        dt = torch.float64 if prm.prec == chym.PREC_FP64 else torch.float32
+        per.append(dict(
+            next_h=0, offs=torch.zeros(R, dtype=torch.int64, device="cuda"),
+            snap=torch.empty(ctx.N * ctx.D * R, dtype=dt, device="cuda"),
+            F=torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda"),
+            E=torch.empty(R, dtype=torch.float64, device="cuda")))
+
+    def advance(steps):
+        if batch is not None:
+            batch.run(prms, scheds, steps, stream)
+        else:
+            for ctx, prm, sched, R in zip(ctxs, prms, scheds, Rs):
+                ctx.run(prm, None, None, steps, sched, stream, n_runs=R)
+
     for _ in range(chunks):
-        ctx.run(prm, None, None, k_dec // 2, sched, stream, n_runs=R)
+        advance(k_dec // 2)
         if net is not None:
-            ctx.copy_state_device(snap.data_ptr(), stream)
-        ctx.run(prm, None, None, k_dec - k_dec // 2, sched, stream, n_runs=R)
-        out.run_steps += R * k_dec
-        k_now = ctx.info()[2]
-        ctx.offsets_device(offs.data_ptr(), stream)
-        local = k_now - offs
-        done = local >= K
-        restart = done.clone()
-        if bool(done.any()):
-            ctx.energy_device(E_dev.data_ptr(), 0, stream)
-            hit = (E_dev - E_gs).abs() <= 1e-9 * max(1.0, abs(E_gs))
-            out.hits += int((hit & done).sum().item())
-            out.completed += int(done.sum().item())
-        if net is not None:
-            at_dec = local == k_dec
-            if bool(at_dec.any()):
-                ctx.features_device(snap.data_ptr(), k_dec / K, F.data_ptr(), stream)
-                z = logits(net, F, stream)
-                retire = at_dec & (z < theta)
-                out.retired += int(retire.sum().item())
-                restart |= retire
-        idx = torch.nonzero(restart).flatten().to(torch.int32)
-        if idx.numel():
-            n = idx.numel()
-            fresh = torch.from_numpy(seed_stream.take(n).view(np.int64)).cuda()
-            pumps = torch.from_numpy(((next_h + np.arange(n)) % n_h).astype(np.int32)).cuda()
-            next_h = (next_h + n) % n_h
-            ctx.reseed_device(idx.data_ptr(), n, fresh.data_ptr(), prm.init_std, pumps.data_ptr(),
-                              stream)
-            torch.cuda.synchronize()
+            for ctx, st in zip(ctxs, per):
+                ctx.copy_state_device(st["snap"].data_ptr(), stream)
+        advance(k_dec - k_dec // 2)
+        for i in range(n):
+            ctx, prm, h, R, st = ctxs[i], prms[i], hs[i], Rs[i], per[i]
+            out.run_steps += R * k_dec
+            k_now = ctx.info()[2]
+            ctx.offsets_device(st["offs"].data_ptr(), stream)
+            local = k_now - st["offs"]
+            done = local >= K
+            restart = done.clone()
+            if bool(done.any()):
+                ctx.energy_device(st["E"].data_ptr(), 0, stream)
+                hit = (st["E"] - E_gss[i]).abs() <= 1e-9 * max(1.0, abs(E_gss[i]))
+                out.hits += int((hit & done).sum().item())
+                out.completed += int(done.sum().item())
+            if net is not None:
+                at_dec = local == k_dec
+                if bool(at_dec.any()):
+                    ctx.features_device(st["snap"].data_ptr(), k_dec / K, st["F"].data_ptr(), stream)
+                    z = logits(net, st["F"], stream)
+                    retire = at_dec & (z < theta)
+                    out.retired += int(retire.sum().item())
+                    restart |= retire
+            idx = torch.nonzero(restart).flatten().to(torch.int32)
+            if idx.numel():
+                m = idx.numel()
+                n_h = len(h)
+                fresh = torch.from_numpy(seed_streams[i].take(m).view(np.int64)).cuda()
+                pumps = torch.from_numpy(((st["next_h"] + np.arange(m)) % n_h).astype(np.int32)).cuda()
+                st["next_h"] = (st["next_h"] + m) % n_h
+                ctx.reseed_device(idx.data_ptr(), m, fresh.data_ptr(), prm.init_std, pumps.data_ptr(),
+                                  stream)
+                torch.cuda.synchronize()
     torch.cuda.synchronize()
     out.seconds = time.perf_counter() - t0
     return out

@@ -73,3 +73,12 @@ def pump_grid(h_th: float, n_h: int, dh_max: float = 1.0) -> np.ndarray:
 def h_per_run(h: np.ndarray, replicas: int) -> np.ndarray:
     """Expand n_h pump values to h-major runs: run = ih * replicas + rep."""
     return np.repeat(np.asarray(h, dtype=np.float64), replicas)
+
+
+def uneven_instances(n_inst: int, seed: int, n_lo: int = 50, n_hi: int = 2000, dims=(2, 3, 4, 8)):
+    """Composition of a batched uneven workload: per instance (N, D, instance seed) with
+    N uniform on the integers [n_lo, n_hi] and D uniform over `dims`."""
+    rng = np.random.default_rng(seed)
+    Ns = rng.integers(n_lo, n_hi + 1, size=n_inst)
+    Ds = rng.choice(np.asarray(dims), size=n_inst)
+    return [(int(N), int(D), int(seed) * 100003 + i) for i, (N, D) in enumerate(zip(Ns, Ds))]

@@ -482,6 +482,97 @@ def test_batch_many_small_instances_against_checker():
     batch.close()
 
 
+def test_batch_tuning_keeps_states_and_results(tmp_path):
+    """chym_batch_tune measures the planner's cost model on the device and restores
+    every state it advanced; a tuned batch (small-N dimensions next to large-N
+    contexts) still equals the contexts integrated alone, and a tuning cache hit
+    sets the cached costs without measuring."""
+    cases = [(100, 2, 4, 20, "mobius"), (60, 3, 4, 9, "sk"), (128, 8, 2, 8, "sk"),
+             (300, 4, 4, 5, "sk"), (611, 2, 2, 7, "sk"), (200, 3, 2, 4, "gauss")]
+    K = 40
+    solo, ctxs, prms, schs = [], [], [], []
+    for i, (N, D, n_h, reps, graph) in enumerate(cases):
+        J, eps, h, seeds = make_case(N, D, n_h, reps, 70 + i, graph)
+        kind = chym.J_REAL if graph == "gauss" else chym.J_PM1
+        prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+        sch = chym.Schedule(1, 20, K)
+        a = chym.Context(J, D, kind)
+        a.run(prm, h, seeds, K, sch)
+        solo.append(a.get_state()[0])
+        a.close()
+        b = chym.Context(J, D, kind)
+        b.run(prm, h, seeds, 5, sch)
+        ctxs.append(b)
+        prms.append(prm)
+        schs.append(sch)
+    before = [c.get_state() for c in ctxs]
+    batch = chym.Batch(ctxs)
+    assert not batch.tuning()["tuned"]
+    cache = str(tmp_path / "tuning.json")
+    t = batch.tune(prms, schs, probe_steps=12, cache_path=cache)
+    assert t["tuned"] and t["k2"] > 0 and all(c > 0 for c in t["chunk"])
+    for (Xb, kb), c in zip(before, ctxs):
+        Xa, ka = c.get_state()
+        assert ka == kb and np.array_equal(Xa, Xb)
+    batch.run(prms, schs, K - 5)
+    batch.status()
+    for Xs, c in zip(solo, ctxs):
+        assert np.array_equal(Xs, c.get_state()[0])
+    # a second batch of the same composition takes the cached costs
+    other = chym.Batch(ctxs)
+    other.set_tuning({"chunk": [1.0] * 8, "k2": 1.0})
+    t2 = other.tune(prms, schs, probe_steps=12, cache_path=cache)
+    assert t2["chunk"] == t["chunk"] and t2["k2"] == t["k2"]
+    with pytest.raises(chym.ChymError):
+        other.set_tuning({"chunk": [1.0] * 7 + [0.0], "k2": 1.0})
+    other.close()
+    batch.close()
+    for c in ctxs:
+        c.close()
+
+
+def test_uneven_batch_full_size_sampled():
+    """The batched uneven workload at its full size: 512 SK +-1 instances with N uniform
+    in [50, 2000] and D in {2, 3, 4, 8}, 64 runs each (16 pumps x 4 replicas), tuned
+    and integrated as one batch for a few steps; one sampled run of every 32nd
+    instance against the oracle.  eps = 0.5 / (2 sqrt(N)), the edge of the SK
+    spectrum."""
+    comp = inputs.uneven_instances(512, 4)
+    K, n_h, reps = 6, 16, 4
+    ctxs, prms, schs, meta = [], [], [], []
+    for N, D, seed in comp:
+        J = inputs.sk_pm1(N, seed)
+        eps = 0.25 / np.sqrt(N)
+        h = inputs.pump_grid(0.5, n_h)
+        seeds = inputs.run_seeds(seed, n_h * reps)
+        c = chym.Context(J, D)
+        prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+        sch = chym.Schedule(1, 3, K)
+        c.run(prm, h, seeds, 0, sch)
+        ctxs.append(c)
+        prms.append(prm)
+        schs.append(sch)
+        meta.append((N, D, seed, h, seeds))
+        del J
+    assert sum(1 for N, _, _ in comp if N <= 128) >= 10
+    batch = chym.Batch(ctxs)
+    batch.tune(prms, schs, probe_steps=2)
+    batch.run(prms, schs, K)
+    batch.status()
+    for i in range(0, 512, 32):
+        N, D, seed, h, seeds = meta[i]
+        X, k = ctxs[i].get_state()
+        assert k == K
+        r = (7 * i) % (n_h * reps)
+        hr = inputs.h_per_run(h, reps)[[r]]
+        Xo = O.run(inputs.sk_pm1(N, seed), D, hr, seeds[[r]], oracle_params(prms[i]),
+                   oracle_schedule(schs[i]), K)
+        assert _rel_err(X[[r]], Xo) <= 1e-4, (N, D)
+    batch.close()
+    for c in ctxs:
+        c.close()
+
+
 # ---------------------------------------------------------------------------
 # retire-and-reseed: a reseeded run follows the trajectory of a fresh run
 # ---------------------------------------------------------------------------
