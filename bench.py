@@ -302,7 +302,9 @@ def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
     false-negative rate on half of a held-out set; the other half measures it.
     Timed: continuous operation (every slot always busy, finished and retired slots
     reseeded) of all contexts as one batch for `chunks` chunks of 10 % of the
-    schedule, with and without the network.  Returns the leg's JSON object."""
+    schedule, with and without the network, after 10 uncounted burn-in chunks (one
+    schedule length) that spread the slots over their schedules.  Returns the leg's
+    JSON object."""
     import torch
     from paper_2308_02329_gb300 import chym
     from paper_2308_02329_gb300 import early_exit as EE
@@ -340,7 +342,8 @@ def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
                                   [j["sched"] for j in jobs], [j["h"] for j in jobs],
                                   [w.runs] * len(jobs), streams, K, k_dec,
                                   [gs[j["name"]] for j in jobs], chunks,
-                                  net if with_net else None, theta, sp, batch=batch)
+                                  net if with_net else None, theta, sp, batch=batch,
+                                  burn_in=10)
     mixed = run(False, 0xC0A7)
     learned = run(True, 0xC0A7)
     net.close()
@@ -352,11 +355,14 @@ def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
            "completed": {"learned": learned.completed, "mixed": mixed.completed},
            "retired": learned.retired, "seconds": {"learned": learned.seconds,
                                                    "mixed": mixed.seconds},
+           "integrate_seconds": {"learned": learned.integrate_seconds,
+                                 "mixed": mixed.integrate_seconds},
            "p_success_completed": {"learned": learned.hits / max(learned.completed, 1),
                                    "mixed": mixed.hits / max(mixed.completed, 1)},
            "fn_rate_heldout": fn, "fn_target": 0.1, "positives_heldout": int(pos.sum()),
            "train_rows": int(F.shape[0]), "train_loss": loss, "setup_s": setup_s,
-           "window": f"{chunks} chunks of {k_dec} steps (decision at 10 % of {K})"}
+           "window": f"{chunks} chunks of {k_dec} steps after 10 uncounted burn-in chunks "
+                     f"(decision at 10 % of {K})"}
     if plain and plain["gs_hits_per_s"] > 0:
         out["ratio_vs_plain_fp32"] = learned.hits_per_second / plain["gs_hits_per_s"]
     return out
@@ -374,8 +380,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--learned-chunks", type=int, default=40,
-                    help="chunks of 10 %% of the schedule in the learned leg's timed window")
+    ap.add_argument("--learned-chunks", type=int, default=30,
+                    help="chunks of 10 %% of the schedule in the learned leg's timed window "
+                         "(after 10 uncounted burn-in chunks)")
     ap.add_argument("--sim-steps", type=int, default=0,
                     help="integration steps per run (default: the workload's); for profiling")
     ap.add_argument("--replicas", type=int, default=0,

@@ -130,6 +130,7 @@ struct K2Runner {
   size_t sig_tiles = 0;
   std::vector<int> sig_dims;
   void* sig_buf = nullptr;
+  int sms = 0;
 };
 }  // namespace chym
 

@@ -29,6 +29,7 @@ class Outcome:
     retired: int = 0
     run_steps: int = 0      # integration steps spent over all slots
     seconds: float = 0.0
+    integrate_seconds: float = 0.0   # of `seconds`, spent in the integration calls
 
     @property
     def hits_per_mstep(self):
@@ -132,10 +133,12 @@ def continuous(ctx, prm, sched, h, R, seed_stream, K, k_dec, E_gs, chunks, net=N
 
 
 def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, chunks,
-                    net=None, theta=-np.inf, stream=0, batch=None):
+                    net=None, theta=-np.inf, stream=0, batch=None, burn_in=0):
     """`continuous` over several contexts at once (one network and threshold for all;
     the features carry N, D and h).  With `batch` (a chym.Batch over ctxs) every chunk
-    of steps is one batched integration of all contexts."""
+    of steps is one batched integration of all contexts.  The first `burn_in` chunks
+    run uncounted and untimed, so that the counted window starts from slots already
+    spread over their schedules (and after first-call costs)."""
     torch = _torch()
     out = Outcome()
     n = len(ctxs)
@@ -152,13 +155,21 @@ def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, c
             E=torch.empty(R, dtype=torch.float64, device="cuda")))
 
     def advance(steps):
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
         if batch is not None:
             batch.run(prms, scheds, steps, stream)
         else:
             for ctx, prm, sched, R in zip(ctxs, prms, scheds, Rs):
                 ctx.run(prm, None, None, steps, sched, stream, n_runs=R)
+        torch.cuda.synchronize()
+        out.integrate_seconds += time.perf_counter() - ta
 
-    for _ in range(chunks):
+    for ci in range(burn_in + chunks):
+        if ci == burn_in:   # start of the counted window
+            torch.cuda.synchronize()
+            out = Outcome()
+            t0 = time.perf_counter()
         advance(k_dec // 2)
         if net is not None:
             for ctx, st in zip(ctxs, per):
