@@ -298,13 +298,16 @@ def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
 
     Setup (untimed): every context generates labelled trajectories with its own fresh
     seeds (features at 10 % of the schedule, outcome at the end), one network is
-    trained on all of them on the GPU, and its retire threshold is set for a 10 %
-    false-negative rate on half of a held-out set; the other half measures it.
-    Timed: continuous operation (every slot always busy, finished and retired slots
-    reseeded) of all contexts as one batch for `chunks` chunks of 10 % of the
-    schedule, with and without the network, after 10 uncounted burn-in chunks (one
-    schedule length) that spread the slots over their schedules.  Returns the leg's
-    JSON object."""
+    trained on all of them on the GPU, and each context gets its own retire
+    threshold, set for a 10 % false-negative rate on half of its held-out runs (no
+    retirement where that half holds fewer than 5 successes); the other half
+    measures the false-negative rate.  Timed: continuous operation (every slot
+    always busy, finished and retired slots reseeded) of all contexts as one batch
+    for `chunks` chunks of 10 % of the schedule, with and without the network, after
+    10 uncounted burn-in chunks (one schedule length) that spread the slots over
+    their schedules.  A context keeps its threshold only where its held-out test
+    half predicts a gain of more than 5 % (early_exit.expected_gain); elsewhere the
+    network is not consulted.  Returns the leg's JSON object."""
     import torch
     from paper_2308_02329_gb300 import chym
     from paper_2308_02329_gb300 import early_exit as EE
@@ -319,21 +322,37 @@ def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
         Fs.append(F)
         ys.append(y)
         F, y, _ = EE.generate(j["ctx"], j["prm"], j["sched"], j["h"],
-                              inputs.run_seeds(0x7A1D0000 + i, w.runs // 2), K, k_dec, gs[j["name"]],
-                              sp)
+                              inputs.run_seeds(0x7A1D0000 + i, w.runs), K, k_dec, gs[j["name"]], sp)
         Fv.append(F)
         yv.append(y)
     F, y = torch.cat(Fs), torch.cat(ys)
     net = chym.MLP(seed=4, max_batch=1024)
     loss = EE.train(net, F, y, epochs=30, batch=512, lr=2e-3, stream=sp)
-    Fv, yv = torch.cat(Fv), torch.cat(yv)
-    sv = EE.logits(net, Fv, sp).cpu().numpy()
-    yvn = yv.cpu().numpy()
-    perm = np.random.default_rng(0).permutation(len(sv))
-    cal, tst = perm[: len(sv) // 2], perm[len(sv) // 2:]
-    theta = EE.threshold_for_fn(sv[cal], yvn[cal], 0.1)
-    pos = yvn[tst] > 0.5
-    fn = float(np.mean(sv[tst][pos] < theta)) if pos.any() else None
+    rng = np.random.default_rng(0)
+    thetas, per_ctx = [], []
+    fn_num = fn_den = 0
+    for i, j in enumerate(jobs):
+        sv = EE.logits(net, Fv[i], sp).cpu().numpy()
+        yvn = yv[i].cpu().numpy()
+        perm = rng.permutation(len(sv))
+        cal, tst = perm[: len(sv) // 2], perm[len(sv) // 2:]
+        pos = yvn[tst] > 0.5
+        th, gain, fn_i, rho_i = -np.inf, None, None, None
+        if int((yvn[cal] > 0.5).sum()) >= 5 and int(pos.sum()) >= 5:
+            th = EE.threshold_for_fn(sv[cal], yvn[cal], 0.1)
+            fn_i = float(np.mean(sv[tst][pos] < th))
+            rho_i = float(np.mean(sv[tst] < th))
+            gain = EE.expected_gain(fn_i, rho_i, k_dec / K)
+            if gain <= 1.05:
+                th = -np.inf
+        if np.isfinite(th):
+            fn_num += int((sv[tst][pos] < th).sum())
+            fn_den += int(pos.sum())
+        thetas.append(th)
+        per_ctx.append({"context": f'{j["name"]}_D{j["D"]}', "p_success": float(yvn.mean()),
+                        "fn_test": fn_i, "retire_frac_test": rho_i, "expected_gain": gain,
+                        "exit_enabled": bool(np.isfinite(th)),
+                        "theta": None if not np.isfinite(th) else float(th)})
     setup_s = time.perf_counter() - t_setup
 
     def run(with_net, key):
@@ -342,7 +361,7 @@ def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
                                   [j["sched"] for j in jobs], [j["h"] for j in jobs],
                                   [w.runs] * len(jobs), streams, K, k_dec,
                                   [gs[j["name"]] for j in jobs], chunks,
-                                  net if with_net else None, theta, sp, batch=batch,
+                                  net if with_net else None, thetas, sp, batch=batch,
                                   burn_in=10)
     mixed = run(False, 0xC0A7)
     learned = run(True, 0xC0A7)
@@ -359,7 +378,8 @@ def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
                                  "mixed": mixed.integrate_seconds},
            "p_success_completed": {"learned": learned.hits / max(learned.completed, 1),
                                    "mixed": mixed.hits / max(mixed.completed, 1)},
-           "fn_rate_heldout": fn, "fn_target": 0.1, "positives_heldout": int(pos.sum()),
+           "fn_rate_heldout": fn_num / fn_den if fn_den else None, "fn_target": 0.1,
+           "positives_heldout": fn_den, "per_context": per_ctx,
            "train_rows": int(F.shape[0]), "train_loss": loss, "setup_s": setup_s,
            "window": f"{chunks} chunks of {k_dec} steps after 10 uncounted burn-in chunks "
                      f"(decision at 10 % of {K})"}

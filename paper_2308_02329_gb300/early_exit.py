@@ -111,6 +111,13 @@ def logits(net, F, stream=0):
     return out
 
 
+def expected_gain(fn, rho, k_frac):
+    """Ground-state hits per integration step with the exit over those without it,
+    when a fraction rho of the runs is retired at the fraction k_frac of the
+    schedule and a fraction fn of the successful runs is among them."""
+    return (1.0 - fn) / (1.0 - (1.0 - k_frac) * rho)
+
+
 def threshold_for_fn(scores, labels, fn_target):
     """Largest threshold whose false-negative rate (successful runs scored below it)
     stays at or below fn_target."""
@@ -133,15 +140,18 @@ def continuous(ctx, prm, sched, h, R, seed_stream, K, k_dec, E_gs, chunks, net=N
 
 
 def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, chunks,
-                    net=None, theta=-np.inf, stream=0, batch=None, burn_in=0):
+                    net=None, theta=-np.inf, stream=0, batch=None, burn_in=0, trace=None):
     """`continuous` over several contexts at once (one network and threshold for all;
     the features carry N, D and h).  With `batch` (a chym.Batch over ctxs) every chunk
     of steps is one batched integration of all contexts.  The first `burn_in` chunks
     run uncounted and untimed, so that the counted window starts from slots already
-    spread over their schedules (and after first-call costs)."""
+    spread over their schedules (and after first-call costs).  `theta` is one
+    threshold or one per context.  With a `trace` list, every chunk appends (chunk,
+    context, decisions, retired, completed, hits)."""
     torch = _torch()
     out = Outcome()
     n = len(ctxs)
+    thetas = list(theta) if np.ndim(theta) else [theta] * n
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     per = []
@@ -172,8 +182,9 @@ def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, c
             t0 = time.perf_counter()
         advance(k_dec // 2)
         if net is not None:
-            for ctx, st in zip(ctxs, per):
-                ctx.copy_state_device(st["snap"].data_ptr(), stream)
+            for ctx, st, th in zip(ctxs, per, thetas):
+                if th > -np.inf:   # contexts without a threshold never retire
+                    ctx.copy_state_device(st["snap"].data_ptr(), stream)
         advance(k_dec - k_dec // 2)
         for i in range(n):
             ctx, prm, h, R, st = ctxs[i], prms[i], hs[i], Rs[i], per[i]
@@ -183,19 +194,26 @@ def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, c
             local = k_now - st["offs"]
             done = local >= K
             restart = done.clone()
+            n_dec = n_ret = n_done = n_hit = 0
             if bool(done.any()):
                 ctx.energy_device(st["E"].data_ptr(), 0, stream)
                 hit = (st["E"] - E_gss[i]).abs() <= 1e-9 * max(1.0, abs(E_gss[i]))
-                out.hits += int((hit & done).sum().item())
-                out.completed += int(done.sum().item())
-            if net is not None:
+                n_hit = int((hit & done).sum().item())
+                n_done = int(done.sum().item())
+                out.hits += n_hit
+                out.completed += n_done
+            if net is not None and thetas[i] > -np.inf:
                 at_dec = local == k_dec
                 if bool(at_dec.any()):
                     ctx.features_device(st["snap"].data_ptr(), k_dec / K, st["F"].data_ptr(), stream)
                     z = logits(net, st["F"], stream)
-                    retire = at_dec & (z < theta)
-                    out.retired += int(retire.sum().item())
+                    retire = at_dec & (z < thetas[i])
+                    n_dec = int(at_dec.sum().item())
+                    n_ret = int(retire.sum().item())
+                    out.retired += n_ret
                     restart |= retire
+            if trace is not None:
+                trace.append((ci, i, n_dec, n_ret, n_done, n_hit))
             idx = torch.nonzero(restart).flatten().to(torch.int32)
             if idx.numel():
                 m = idx.numel()
