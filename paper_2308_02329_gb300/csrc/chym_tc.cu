@@ -248,10 +248,22 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint4* __restrict__ rk
   return c;
 }
 
+// SFU approximations with denormals flushed: no argument or result of the noise
+// transform is denormal, so they equal the non-flushing forms there, in fewer
+// instructions.
 __device__ __forceinline__ float sqrt_approx(float x) {
   float r;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void sincos_approx(float x, float& s, float& c) {
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
 // Box-Muller for two runs at once: words (wr, wa) of run A and of run B give
@@ -267,12 +279,12 @@ __device__ __forceinline__ void box_muller_x2(uint32_t wrA, uint32_t waA, uint32
   const float2 ang_c = make_float2(-3.1415926528582302f, -3.1415926528582302f);
   const float2 ur = __ffma2_rn(make_float2((float)wrA, (float)wrB), two32, half32);
   const float2 th = __ffma2_rn(make_float2((float)waA, (float)waB), ang_m, ang_c);
-  const float2 r2 = __fmul2_rn(make_float2(__log2f(ur.x), __log2f(ur.y)),
+  const float2 r2 = __fmul2_rn(make_float2(lg2_approx(ur.x), lg2_approx(ur.y)),
                                make_float2(neg2ln2s2, neg2ln2s2));
   const float2 r = make_float2(-sqrt_approx(r2.x), -sqrt_approx(r2.y));
   float sA, cA, sB, cB;
-  __sincosf(th.x, &sA, &cA);
-  __sincosf(th.y, &sB, &cB);
+  sincos_approx(th.x, sA, cA);
+  sincos_approx(th.y, sB, cB);
   zc = __fmul2_rn(r, make_float2(cA, cB));
   zs = __fmul2_rn(r, make_float2(sA, sB));
 }
