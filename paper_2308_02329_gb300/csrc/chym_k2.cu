@@ -139,12 +139,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (+)= A B on the tensor core, kind::f16 (BF16 operands, FP32 accumulator), with
+// both shared-memory descriptors given by their low words (their high words are
+// equal).
+__device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi,
+                                           uint32_t idesc, uint32_t accumulate) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+      "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+      "mov.b64 da, {%1, %3};\n\tmov.b64 db, {%2, %3};\n\t"
+      "setp.ne.b32 p, %5, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -301,12 +306,16 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
       for (int t = blockIdx.x; t < L.n_tiles && !s_abort; t += gridDim.x) {
         const K2Tile tile = L.tiles[t];
         const K2Desc& d = L.descs[tile.desc];
+        // the tile's constants in registers (the loop's asm statements clobber memory)
+        const int KC = d.KC, terms = d.a_terms;
         const uint32_t BB = b_block_bytes(d.n);
-        const uint32_t bytes = (uint32_t)d.a_terms * kABlock + 2u * BB;
-        const uint8_t* Xt_cur = d.Xt + (size_t)(step & 1) * d.buf_bytes;
-        const size_t lo_off = (size_t)d.CT * d.KC * BB;
+        const uint32_t bytes = (uint32_t)terms * kABlock + 2u * BB;
+        const uint8_t* a_src = d.Aimg + (size_t)tile.mt * KC * kABlock;       // term 0, K chunk 0
+        const size_t a_term = (size_t)d.MT * KC * kABlock;                    // to the residual term
+        const uint8_t* b_src = d.Xt + (size_t)(step & 1) * d.buf_bytes + (size_t)tile.ct * KC * BB;
+        const size_t lo_off = (size_t)d.CT * KC * BB;
         bool stop = false;
-        for (int kc = 0; kc < d.KC; ++kc, ++g) {
+        for (int kc = 0; kc < KC; ++kc, ++g, a_src += kABlock, b_src += BB) {
           const uint32_t s = g % (uint32_t)S;
           if (g >= (uint32_t)S && !mbar_wait(smem_addr(&empty_bar[s]), ((g / S) - 1u) & 1u)) {
             atomicOr(L.status, STATUS_TIMEOUT);
@@ -318,13 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
           const uint32_t fb = smem_addr(&full_bar[s]);
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes)
                        : "memory");
-          for (int a = 0; a < d.a_terms; ++a)
-            bulk_g2s(base + (uint32_t)a * kABlock,
-                     d.Aimg + ((size_t)(a * d.MT + tile.mt) * d.KC + kc) * kABlock, kABlock, fb);
-          const size_t blk = ((size_t)tile.ct * d.KC + kc) * BB;
-          const uint32_t bb = base + (uint32_t)d.a_terms * kABlock;
-          bulk_g2s(bb, Xt_cur + blk, BB, fb);
-          bulk_g2s(bb + BB, Xt_cur + lo_off + blk, BB, fb);
+          bulk_g2s(base, a_src, kABlock, fb);
+          if (terms > 1) bulk_g2s(base + kABlock, a_src + a_term, kABlock, fb);
+          const uint32_t bb = base + (uint32_t)terms * kABlock;
+          bulk_g2s(bb, b_src, BB, fb);
+          bulk_g2s(bb + BB, b_src + lo_off, BB, fb);
         }
         if (stop) break;
       }
@@ -352,23 +359,29 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) |
                                ((uint32_t)(d.n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         const uint32_t acc = tmem + b * (uint32_t)kAccCols;
-        for (int kc = 0; kc < d.KC; ++kc, ++g) {
+        // Descriptors as two 32-bit words: the low word (start address >> 4, LBO)
+        // is the only part that moves between stages and K steps, so each product
+        // costs one add; the high word (SBO, version) is the same for all of them.
+        const uint32_t d_hi = (uint32_t)(smem_desc(0u, kCoreK, kCoreMN) >> 32);
+        const uint32_t d_lo0 = (uint32_t)smem_desc(smem_addr(smem), kCoreK, kCoreMN);
+        const uint32_t o_bhi = ((uint32_t)d.a_terms * kABlock) >> 4, o_blo = o_bhi + (BB >> 4);
+        const uint32_t o_alo = kABlock >> 4, stride16 = L.stage_stride >> 4;
+        const bool real_j = d.a_terms > 1;
+        const int KC = d.KC;
+        for (int kc = 0; kc < KC; ++kc, ++g) {
           const uint32_t s = g % (uint32_t)S;
           if (!mbar_wait(smem_addr(&full_bar[s]), (g / S) & 1u) || s_abort) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t base = smem_addr(smem) + s * L.stage_stride;
-          const uint32_t bhi = base + (uint32_t)d.a_terms * kABlock, blo = bhi + BB;
+          const uint32_t a0 = d_lo0 + s * stride16;
 #pragma unroll
           for (int ks = 0; ks < kKc / 16; ++ks) {
-            const uint32_t o = (uint32_t)ks * 2u * kCoreK;
-            const uint64_t da = smem_desc(base + o, kCoreK, kCoreMN);
-            const uint64_t dh = smem_desc(bhi + o, kCoreK, kCoreMN);
-            mma_bf16(acc, da, dh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-            mma_bf16(acc, da, smem_desc(blo + o, kCoreK, kCoreMN), idesc, 1u);
-            if (d.a_terms > 1) mma_bf16(acc, smem_desc(base + kABlock + o, kCoreK, kCoreMN), dh, idesc, 1u);
+            const uint32_t a = a0 + (uint32_t)ks * (2u * kCoreK >> 4);
+            mma_bf16_w(acc, a, a + o_bhi, d_hi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+            mma_bf16_w(acc, a, a + o_blo, d_hi, idesc, 1u);
+            if (real_j) mma_bf16_w(acc, a + o_alo, a + o_bhi, d_hi, idesc, 1u);
           }
           mma_commit(smem_addr(&empty_bar[s]));
         }
@@ -403,8 +416,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
       uint8_t* Xt_next = dref.Xt + (size_t)((step + 1) & 1) * dref.buf_bytes;
       const size_t lo_off = (size_t)dref.CT * dref.KC * BB;
       // byte offset of this thread's spin (row k = p of the next step's B) in its block
-      const size_t row_off = ((size_t)tile.ct * dref.KC + (p >> 5)) * BB +
-                             (size_t)((p & 31) >> 3) * kCoreK + (size_t)(p & 7) * 16u;
+      const size_t row_off = ((size_t)tile.ct * dref.KC + (p / kKc)) * BB +
+                             (size_t)((p % kKc) >> 3) * kCoreK + (size_t)(p & 7) * 16u;
       const int run_tile = tile.ct * RT;
       float xc[D][kRB];
       load_block_x<D>(Xm, KP, n_runs, run_tile + kRB * e, p, live, xc);  // in flight during the products
