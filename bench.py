@@ -79,24 +79,46 @@ WORKLOADS = {
     "uneven": Workload("uneven", "512 SK+-1 instances, N uniform in [50, 2000], D uniform in "
                        "{2,3,4,8}, 64 runs each (16 h x 4 replicas), 30000 steps dt=0.01, "
                        "one tuned batch", [], (2, 3, 4, 8), 16, 4, 30000, compare_plain=False),
+    "fig4": Workload("fig4", "size scaling of Fig. 4: 20 % sparse +-1 graphs, N = 10..100, 16 graphs "
+                     "per N; CIM (D=1, 51 h) and CHYM+DA (D=2 annealed, 21 h), 32 replicas, "
+                     "20000 steps dt=0.01", [], (1, 2), 21, 32, 20000, compare_plain=False),
 }
+FIG4_NS = tuple(range(10, 101, 10))
+FIG4_GRAPHS = 16
 UNEVEN_INSTANCES = 512
 
 
 def workload_specs(w, rank):
-    """(name, graph kind, N, D, instance seed or None) of every context of a workload."""
+    """Every context of a workload: name, graph kind, N, D, instance seed (or None),
+    pump values, replicas and the machine constants (gamma, kappa, schedule kind)."""
+    def spec(name, kind, N, D, seed, n_h=None, gamma=25.0, mode=None):
+        kappa, skind = mode if mode else mode_for(D)
+        return {"name": name, "kind": kind, "N": N, "D": D, "seed": seed,
+                "n_h": n_h or w.n_h, "reps": w.reps, "gamma": gamma, "kappa": kappa, "skind": skind}
     if w.key == "uneven":
         from paper_2308_02329_gb300 import inputs
         comp = inputs.uneven_instances(UNEVEN_INSTANCES, INSTANCE_SEED + 4)
-        return [(f"sk{N}_{i}", "sk", N, D, seed + 1000003 * rank)
+        return [spec(f"sk{N}_{i}", "sk", N, D, seed + 1000003 * rank)
                 for i, (N, D, seed) in enumerate(comp)]
-    return [(name, kind, N, D, None) for name, kind, N in w.graphs for D in w.D]
+    if w.key == "fig4":
+        from paper_2308_02329_gb300 import scaling
+        out = []
+        for N, g, seed in scaling.graph_set(FIG4_NS, FIG4_GRAPHS, seed=0x5CA1E + 7 * rank):
+            for mode, m in scaling.MODES.items():
+                out.append(spec(f"sparse{N}_{g}", "sparse", N, m["D"], seed,
+                                n_h=51 if m["D"] == 1 else 21, gamma=m["gamma"],
+                                mode=(m["kappa"], 1 if m["anneal"] else 0)))
+                out[-1]["mode"] = mode
+        return out
+    return [spec(name, kind, N, D, None) for name, kind, N in w.graphs for D in w.D]
 
 
 def build_graph(kind, N, rank, seed=None):
     from paper_2308_02329_gb300 import inputs
     if kind == "moebius":
         return inputs.mobius_ladder(N)
+    if kind == "sparse":
+        return inputs.sparse_pm1(N, 0.2, seed)
     if kind == "sk":
         return inputs.sk_pm1(N, seed if seed is not None else INSTANCE_SEED + 1 + 1000 * rank)
     return inputs.gaussian(N, INSTANCE_SEED + 2 + 1000 * rank)
@@ -111,8 +133,12 @@ def mode_for(D):
 
 
 def workload_config(w, prec_name, sim_steps):
-    graphs = ([f"{n}_{N}" for n, _, N in w.graphs] if w.graphs else
-              [f"{UNEVEN_INSTANCES} SK+-1 instances, N in [50, 2000]"])
+    if w.graphs:
+        graphs = [f"{n}_{N}" for n, _, N in w.graphs]
+    elif w.key == "fig4":
+        graphs = [f"{FIG4_GRAPHS} sparse +-1 graphs (density 0.2) per N in {list(FIG4_NS)}"]
+    else:
+        graphs = [f"{UNEVEN_INSTANCES} SK+-1 instances, N in [50, 2000]"]
     return {"workload": w.title, "key": w.key, "graphs": graphs, "D": list(w.D),
             "runs_per_graph": w.runs, "n_h": w.n_h, "replicas": w.reps, "steps": sim_steps,
             "precision": prec_name, "l2": "flushed between steps (256 MiB write)"}
@@ -218,18 +244,19 @@ def oracle_jobs(w):
     import oracle.oracle as O
     jobs = []
     specs = workload_specs(w, 0)
-    if w.key == "uneven":
+    if w.key in ("uneven", "fig4"):
         specs = specs[::32]
     cache = {}
-    for name, kind, N, D, seed in specs:
+    for sp in specs:
+        kind, N, seed = sp["kind"], sp["N"], sp["seed"]
         if (kind, N, seed) not in cache:
             J = build_graph(kind, N, 0, seed)
-            cache[(kind, N, seed)] = (J, float(np.linalg.eigvalsh(J)[-1]))
+            lam = float(np.linalg.eigvalsh(J)[-1])
+            cache[(kind, N, seed)] = (J, lam if lam > 0 else 1.0)
         J, lam = cache[(kind, N, seed)]
-        kappa, skind = mode_for(D)
-        prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=kappa,
+        prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=sp["gamma"], kappa=sp["kappa"],
                        eps=EPS_HAT / lam)
-        jobs.append((J, D, prm, O.Schedule(skind, w.steps // 2, w.steps)))
+        jobs.append((J, sp["D"], prm, O.Schedule(sp["skind"], w.steps // 2, w.steps)))
     return jobs
 
 
@@ -434,7 +461,8 @@ def main():
     # ---------------- setup (untimed): instances, references, device inputs ----------
     jobs, gs = [], {}
     graphs = {}
-    for gi, (name, kind, N, D, seed) in enumerate(workload_specs(w, rank)):
+    for gi, sp in enumerate(workload_specs(w, rank)):
+        name, kind, N, D, seed = sp["name"], sp["kind"], sp["N"], sp["D"], sp["seed"]
         if name not in graphs:
             J = build_graph(kind, N, rank, seed)
             graphs[name] = J
@@ -443,23 +471,28 @@ def main():
                 gs[name] = chym.ground_state_mobius(N)
             elif w.key == "uneven":
                 gs[name] = float("inf")    # best energy of the warm-up runs (below)
+            elif kind == "sparse" and N <= 24:
+                c1 = chym.Context(J, 1, jkind)
+                gs[name] = c1.ground_state_exact()[0]
+                c1.close()
             else:
                 c1 = chym.Context(J, 1, jkind)
-                restarts, sweeps = (64, 2000) if N <= 200 else (4, 400)
+                restarts, sweeps = ((16, 1000) if kind == "sparse" else (64, 2000)) if N <= 200 else (4, 400)
                 gs[name] = c1.ground_state_search(restarts=restarts, sweeps=sweeps, seed=11)[0]
                 c1.close()
         J = graphs[name]
         jkind = chym.J_REAL if kind == "gauss" else chym.J_PM1
         ctx = chym.Context(J, D, jkind)
-        kappa, skind = mode_for(D)
-        h = inputs.pump_grid(1.0 - EPS_HAT, w.n_h)
-        sd = INSTANCE_SEED + 7919 * rank + 97 * gi + D if seed is None else seed
-        seeds = inputs.run_seeds(sd, w.runs)
-        jobs.append(dict(name=name, N=N, D=D, ctx=ctx, kappa=kappa, skind=skind, h=h,
+        n_h, runs = sp["n_h"], sp["n_h"] * sp["reps"]
+        h = inputs.pump_grid(1.0 - EPS_HAT, n_h)
+        sd = INSTANCE_SEED + 7919 * rank + 97 * gi + D if seed is None else seed + D
+        seeds = inputs.run_seeds(sd, runs)
+        jobs.append(dict(name=name, N=N, D=D, ctx=ctx, kappa=sp["kappa"], skind=sp["skind"],
+                         gamma=sp["gamma"], mode=sp.get("mode"), n_h=n_h, runs=runs, h=h,
                          seeds=seeds, d_h=torch.from_numpy(h).to(dev),
                          d_seeds=torch.from_numpy(seeds.view(np.int64)).to(dev),
-                         d_E=torch.empty(w.runs, dtype=torch.float64, device=dev),
-                         nnz=int((J != 0).sum(1).mean())))
+                         d_E=torch.empty(runs, dtype=torch.float64, device=dev),
+                         nnz=max(1, int((J != 0).sum(1).mean()))))
         if w.key == "uneven":
             del graphs[name]     # the context holds its own copy of J
     # lambda_max of every context (host Lanczos; ctypes releases the GIL)
@@ -467,8 +500,8 @@ def main():
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as pool:
         lams = list(pool.map(lambda j: j["ctx"].lambda_max(), jobs))
     for j, lam in zip(jobs, lams):
-        j["prm"] = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=25.0, kappa=j["kappa"],
-                               eps=EPS_HAT / lam, prec=prec)
+        j["prm"] = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=j["gamma"], kappa=j["kappa"],
+                               eps=EPS_HAT / lam if lam > 0 else 0.0, prec=prec)
         j["sched"] = chym.Schedule(j["skind"], sim_steps // 2 if j["skind"] else 0, sim_steps)
     graphs.clear()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -479,8 +512,8 @@ def main():
     if w.key == "uneven":
         # the planner's cost model, measured for this batch (setup, untimed)
         for j in jobs:
-            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), w.n_h, j["d_seeds"].data_ptr(),
-                                w.runs, 0, j["sched"], stream.cuda_stream)
+            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), j["n_h"], j["d_seeds"].data_ptr(),
+                                j["runs"], 0, j["sched"], stream.cuda_stream)
         tuning = batch.tune([j["prm"] for j in jobs], [j["sched"] for j in jobs],
                             probe_steps=32, stream=stream.cuda_stream)
 
@@ -491,8 +524,8 @@ def main():
         flush.fill_(1.0)
         sp = stream.cuda_stream
         for j in jobs:
-            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), w.n_h, j["d_seeds"].data_ptr(),
-                                w.runs, 0, j["sched"], sp)
+            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), j["n_h"], j["d_seeds"].data_ptr(),
+                                j["runs"], 0, j["sched"], sp)
         e0 = torch.cuda.Event(enable_timing=record)
         e1 = torch.cuda.Event(enable_timing=record)
         e0.record(stream)
@@ -543,7 +576,7 @@ def main():
     clocks.start()
     elapsed, hits_total = timed_region(args.steps)
     clock_info = clocks.stop()
-    work_step = sum(j["N"] * j["D"] * w.runs * sim_steps for j in jobs)
+    work_step = sum(j["N"] * j["D"] * j["runs"] * sim_steps for j in jobs)
     value = work_step * args.steps * world / elapsed
 
     # roofline of the dominant kernel (the step kernels of the batch, concurrent):
@@ -556,9 +589,9 @@ def main():
     peaks, peak_src = measured_peaks()
     large = max(j["N"] for j in jobs) > 128 and prec == chym.PREC_BF16X2
     if large:
-        alg = args.steps * sum(2.0 * j["N"] ** 2 * j["D"] * w.runs * sim_steps for j in jobs)
+        alg = args.steps * sum(2.0 * j["N"] ** 2 * j["D"] * j["runs"] * sim_steps for j in jobs)
         issued = args.steps * sum(
-            2.0 * (128 * -(-j["N"] // 128)) ** 2 * j["D"] * w.runs * sim_steps *
+            2.0 * (128 * -(-j["N"] // 128)) ** 2 * j["D"] * j["runs"] * sim_steps *
             (2 if j["name"] != "gauss" else 3) for j in jobs)
         peak = peaks["bf16_tflops_sustained"] * 1e12
         roofline = {"bound": "tensor", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
@@ -570,7 +603,7 @@ def main():
         on_alu = prec == chym.PREC_FP32
         alg = args.steps * sum(
             alu_ops_per_element(j["D"], j["N"] if j["name"] == "sk" else j["nnz"], on_alu) *
-            j["N"] * j["D"] * w.runs * sim_steps for j in jobs)
+            j["N"] * j["D"] * j["runs"] * sim_steps for j in jobs)
         sm_mhz = clock_info.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * sm_mhz * 1e6
         roofline = {"bound": "alu", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
@@ -594,7 +627,7 @@ def main():
     if not args.no_e2e:
         pin_h = [torch.from_numpy(j["h"]).pin_memory() for j in jobs]
         pin_s = [torch.from_numpy(j["seeds"].view(np.int64)).pin_memory() for j in jobs]
-        E_host = [torch.empty(w.runs, dtype=torch.float64).pin_memory() for _ in jobs]
+        E_host = [torch.empty(j["runs"], dtype=torch.float64).pin_memory() for j in jobs]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -612,10 +645,32 @@ def main():
         el2 = time.perf_counter() - t0
         if world > 1:
             el2, _ = merge_over_ranks(el2, 0, dist, dev)
-        h2d = sum(w.n_h * 8 + w.runs * 8 for _ in jobs)
-        d2h = sum(w.runs * 8 + 64 + w.n_h * 8 for _ in jobs)
+        h2d = sum(j["n_h"] * 8 + j["runs"] * 8 for j in jobs)
+        d2h = sum(j["runs"] * 8 + 64 + j["n_h"] * 8 for j in jobs)
         e2e = {"value": work_step * args.steps * world / el2, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---------------- Fig. 4: size scaling of the success probability ----------------
+    scaling_study = None
+    if w.key == "fig4":
+        from paper_2308_02329_gb300 import scaling
+        rows = {}
+        for j in jobs:   # figures of the last timed step's runs
+            st = j["ctx"].stats(gs[j["name"]], 0, stream.cuda_stream)
+            g = int(j["name"].split("_")[1])
+            rows.setdefault(j["mode"], []).append(scaling.GraphResult(
+                j["N"], g, float(gs[j["name"]]), j["N"] <= 24, float(st["P_max"]),
+                float(st["W_range"]), float(st["W_scan"]), float(st["dE_mean"])))
+        scaling_study = {}
+        for mode, rs in rows.items():
+            agg = scaling.aggregate(rs)
+            a, c, used = scaling.fit_exponential(list(agg), [agg[N]["P_max"]["mean"] for N in agg])
+            scaling_study[mode] = {"decay_a": a, "decay_c": c, "fit_points": used,
+                                   "P_max_mean": {str(N): agg[N]["P_max"]["mean"] for N in agg},
+                                   "P_max_iqr": {str(N): [agg[N]["P_max"]["q25"], agg[N]["P_max"]["q75"]]
+                                                 for N in agg},
+                                   "W_range_mean": {str(N): agg[N]["W_range"]["mean"] for N in agg},
+                                   "dE_mean": {str(N): agg[N]["dE_mean"]["mean"] for N in agg}}
 
     # ---------------- mixed + learned early exit (continuous operation) ----------------
     learned = None
@@ -652,6 +707,8 @@ def main():
                 "gpu_launches": args.steps * per_step}
         if tuning is not None:
             line["tuning"] = tuning
+        if scaling_study is not None:
+            line["scaling_study"] = scaling_study
         if learned is not None:
             line["learned"] = learned
             line["gs_hits_ratio_learned_vs_plain"] = learned.get("ratio_vs_plain_fp32")

@@ -25,7 +25,7 @@
 //   warp 1  MMA issuer: tcgen05.mma (M = 128, N = n, K = 16), J_hi X_hi +
 //           J_hi X_lo (+ J_lo X_hi), FP32 accumulators in TMEM, two of them so
 //           that the next tile's products run while the epilogue drains the last;
-//   warps 2-17 epilogue: thread = spin (TMEM lane) x a quarter of the tile's runs; it
+//   warps 2-9  epilogue: thread = spin (TMEM lane) x half of the tile's runs; it
 //           loads its runs' x (global) before the accumulator is ready, then reads
 //           Y (tcgen05.ld), applies drift, loss, annealing and Philox noise (text
 //           after Eq. 1 and after Fig. 2), writes x back and the new BF16 hi/lo
@@ -51,7 +51,7 @@ constexpr uint32_t kABlock = 128 * kKc * 2;    // bytes of an A block (8 KB)
 constexpr uint32_t kCoreK = 128;               // K-direction core stride (both operands)
 constexpr uint32_t kCoreMN = (kKc / 8) * 128;  // M/N-direction core stride (512)
 constexpr int kMaxStages = 8;
-constexpr int kWQ = 4;                         // epilogue warps per TMEM lane quarter
+constexpr int kWQ = 2;                         // epilogue warps per TMEM lane quarter
 constexpr int kEpiWarps = 4 * kWQ;
 constexpr int kRB = 4;                         // runs of one epilogue block
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer + MMA + epilogue
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
       if (!mbar_wait(smem_addr(&drain_bar), 0u)) atomicOr(L.status, STATUS_TIMEOUT);
     }
   } else {
-    // ---------------- epilogue: 16 warps ----------------
+    // ---------------- epilogue: 4 kWQ warps ----------------
     const int q = warp & 3;             // TMEM lane quarter of this warp
     const int e = (warp - 2) >> 2;      // its 4-run blocks: rb = e, e + kWQ, e + 2 kWQ, ...
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
