@@ -158,13 +158,16 @@ def alu_ops_per_element(D, nnz_row, coupling_on_alu):
     """Algorithmic ALU lane-operations per element-step (one x_{p,mu} advanced once).
 
     Noise: one Philox4x32-10 block (10 rounds x [2 wide multiplies + 2 three-input
-    xors + 2 key adds] = 60 ops) per spin per 4 components, Box-Muller 12 ops per pair
+    xors + 2 key adds] = 60 ops) per four normals (per spin and 4 components for D >= 3,
+    per 4/D spins for D <= 2), Box-Muller 12 ops per pair
     (2 int->float, 2 scalings, log, radius scaling, sqrt, angle, sin, cos, 2 products).
     Drift + Euler-Maruyama update: 6.5 ops (norm share, x^2, cubic/loss FMA, product,
     coupling FMA, noise add).  Coupling on the ALU adds nnz_row FMAs (dense J: N)."""
-    blocks = -(-D // 4)
-    pairs = -(-D // 2)
-    ops = 60.0 * blocks / D + 12.0 * pairs / D + 6.5
+    if D <= 2:      # the 4/D spins of a Philox block share it (all four normals used)
+        blocks_per_el, pairs_per_el = 0.25, 0.5
+    else:
+        blocks_per_el, pairs_per_el = -(-D // 4) / D, -(-D // 2) / D
+    ops = 60.0 * blocks_per_el + 12.0 * pairs_per_el + 6.5
     if coupling_on_alu:
         ops += nnz_row
     return ops
@@ -508,14 +511,14 @@ def main():
     streams = [torch.cuda.Stream(dev) for _ in jobs]
     batch = chym.Batch([j["ctx"] for j in jobs])
     spans = []
+    # the planner's cost model, measured for this batch on this device (setup, untimed)
+    for j in jobs:
+        j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), j["n_h"], j["d_seeds"].data_ptr(),
+                            j["runs"], 0, j["sched"], stream.cuda_stream)
     tuning = None
-    if w.key == "uneven":
-        # the planner's cost model, measured for this batch (setup, untimed)
-        for j in jobs:
-            j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), j["n_h"], j["d_seeds"].data_ptr(),
-                                j["runs"], 0, j["sched"], stream.cuda_stream)
+    if prec == chym.PREC_BF16X2:
         tuning = batch.tune([j["prm"] for j in jobs], [j["sched"] for j in jobs],
-                            probe_steps=32, stream=stream.cuda_stream)
+                            probe_steps=min(256, sim_steps), stream=stream.cuda_stream)
 
     def one_step(record=False):
         """init every (graph, D), integrate all of them together as one batch (persistent

@@ -79,22 +79,34 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
 /* Gaussian noise of the method (reading: additive Gaussian noise per PO).   */
 /*                                                                           */
 /* For run seed s, stream tag t (0: per-step noise, 1: initial state), step  */
-/* k, spin p and component mu: key = (lo32 s, hi32 s), counter =             */
-/* (p, (t << 8) | (mu / 4), lo32 k, hi32 k).  The four 32-bit words become    */
+/* k, spin p and component mu of a D-component hyperspin: key = (lo32 s,     */
+/* hi32 s).  One Philox4x32-10 block gives four normals:                     */
+/*   D >= 3: counter (p, (t << 8) | (mu / 4), lo32 k, hi32 k), normal mu % 4; */
+/*   D <= 2: the 4/D spins p with the same p / (4/D) share one block,        */
+/*           counter (p / (4/D), t << 8, lo32 k, hi32 k), normal number      */
+/*           (p % (4/D)) * D + mu (so every normal of the block is used).    */
+/* (For D = 4 the two rules coincide.)  The four 32-bit words become         */
 /* uniforms u_j = (w_j + 1/2) 2^-32 in (0,1); Box-Muller turns (u0,u1) into   */
-/* (r cos 2 pi u1, r sin 2 pi u1) with r = sqrt(-2 ln u0), likewise (u2,u3);  */
-/* component mu takes normal number mu mod 4 of its block.                   */
+/* (r cos 2 pi u1, r sin 2 pi u1) with r = sqrt(-2 ln u0), likewise (u2,u3).  */
 /* ------------------------------------------------------------------------ */
 #define ORACLE_TWO_PI 6.283185307179586476925286766559
 
 double oracle_normal(uint64_t seed, uint32_t tag, uint64_t k, uint32_t p,
-                     uint32_t mu) {
-  uint32_t ctr[4] = {p, (tag << 8) | (mu / 4u), (uint32_t)k,
+                     uint32_t mu, uint32_t D) {
+  uint32_t block, j;
+  if (D <= 2u) {
+    const uint32_t per = 4u / D; /* spins per block */
+    block = p / per;
+    j = (p % per) * D + mu;
+  } else {
+    block = p;
+    j = mu % 4u;
+  }
+  uint32_t ctr[4] = {block, (tag << 8) | (D <= 2u ? 0u : mu / 4u), (uint32_t)k,
                      (uint32_t)(k >> 32)};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t w[4];
   oracle_philox4x32_10(ctr, key, w);
-  uint32_t j = mu % 4u;
   uint32_t pair = j / 2u; /* 0: words (0,1), 1: words (2,3) */
   double u_r = ((double)w[2 * pair] + 0.5) / 4294967296.0;
   double u_a = ((double)w[2 * pair + 1] + 0.5) / 4294967296.0;
@@ -128,7 +140,7 @@ void oracle_init(int N, int D, int n_runs, const uint64_t* seeds,
     for (int p = 0; p < N; ++p)
       for (int mu = 0; mu < D; ++mu)
         X[((size_t)r * N + p) * D + mu] =
-            init_std * oracle_normal(seeds[r], 1u, 0u, (uint32_t)p, (uint32_t)mu);
+            init_std * oracle_normal(seeds[r], 1u, 0u, (uint32_t)p, (uint32_t)mu, (uint32_t)D);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -188,7 +200,7 @@ void oracle_integrate(const double* J, int N, int D, int n_runs,
         for (int p = 0; p < N; ++p)
           for (int mu = 0; mu < D; ++mu) {
             double xi = oracle_normal(seeds[r], 0u, (uint64_t)k, (uint32_t)p,
-                                      (uint32_t)mu);
+                                      (uint32_t)mu, (uint32_t)D);
             x[(size_t)p * D + mu] += dt * f[(size_t)p * D + mu] + noise_scale * xi;
           }
       }
@@ -325,5 +337,5 @@ void oracle_normals(uint64_t seed, uint32_t tag, uint64_t k, int N, int D,
                     double* out) {
   for (int p = 0; p < N; ++p)
     for (int mu = 0; mu < D; ++mu)
-      out[(size_t)p * D + mu] = oracle_normal(seed, tag, k, (uint32_t)p, (uint32_t)mu);
+      out[(size_t)p * D + mu] = oracle_normal(seed, tag, k, (uint32_t)p, (uint32_t)mu, (uint32_t)D);
 }

@@ -25,7 +25,7 @@ def _L():
         u64p = ctypes.POINTER(ctypes.c_uint64)
         lib.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
         lib.oracle_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
-                                      ctypes.c_uint32, ctypes.c_uint32]
+                                      ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
         lib.oracle_normal.restype = ctypes.c_double
         lib.oracle_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                        ctypes.c_int, ctypes.c_int, dp]
@@ -94,8 +94,9 @@ def philox4x32_10(ctr, key):
     return out
 
 
-def normal(seed, tag, k, p, mu):
-    return _L().oracle_normal(int(seed), int(tag), int(k), int(p), int(mu))
+def normal(seed, tag, k, p, mu, D):
+    """Normal of component mu of spin p of a D-component run (see oracle_normal)."""
+    return _L().oracle_normal(int(seed), int(tag), int(k), int(p), int(mu), int(D))
 
 
 def normals(seed, tag, k, N, D):

@@ -484,10 +484,22 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
           for (int j = 0; j < kRB; ++j) {
             const RunC c = rcb[j];
             const bool ok_run = live && run0 + j < n_runs;
-            const uint4 w = philox_wide(make_uint4((uint32_t)p, (uint32_t)blk, c.kl_lo, c.kl_hi), c.key0, c.key1);
             float z[4];
-            box_muller(w.x, w.y, nl2, z[0], z[1]);
-            if (M > 2) box_muller(w.z, w.w, nl2, z[2], z[3]);
+            if constexpr (D <= 2) {
+              // the 4/D spins with the same p / (4/D) share one block; spin p takes its
+              // normals (p % (4/D)) D .. + D - 1, one Box-Muller pair
+              constexpr uint32_t per = 4u / D;
+              const uint4 w = philox_wide(make_uint4((uint32_t)p / per, 0u, c.kl_lo, c.kl_hi), c.key0, c.key1);
+              const uint32_t j0 = ((uint32_t)p % per) * D;
+              float cz, sz;
+              box_muller(j0 >= 2u ? w.z : w.x, j0 >= 2u ? w.w : w.y, nl2, cz, sz);
+              z[0] = (j0 & 1u) ? sz : cz;
+              z[1] = sz;
+            } else {
+              const uint4 w = philox_wide(make_uint4((uint32_t)p, (uint32_t)blk, c.kl_lo, c.kl_hi), c.key0, c.key1);
+              box_muller(w.x, w.y, nl2, z[0], z[1]);
+              if (M > 2) box_muller(w.z, w.w, nl2, z[2], z[3]);
+            }
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
               if (m < M) {

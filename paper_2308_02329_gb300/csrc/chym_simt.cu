@@ -28,10 +28,29 @@ struct SimtTraits<float> {
 };
 
 // Normal numbers of spin p for components 0..D-1 at step k (tag 0 or 1).
+// For D <= 2 the 4/D spins with the same p / (4/D) share one Philox block: spin p
+// takes the normals (p % (4/D)) * D .. + D - 1 of it (one Box-Muller pair).
 template <typename T, int D>
 __device__ __forceinline__ void spin_normals(uint64_t seed, uint32_t tag, uint64_t k, int p,
                                              T scale, T z[D]) {
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  if constexpr (D <= 2) {
+    constexpr uint32_t per = 4u / D;
+    const uint4 w = philox4x32_10(noise_counter((uint32_t)p / per, 0u, tag, k), k0, k1);
+    const uint32_t j0 = ((uint32_t)p % per) * D;  // first normal of this spin in the block
+    const uint32_t wr = j0 >= 2u ? w.z : w.x, wa = j0 >= 2u ? w.w : w.y;
+    T c, sn;
+    if constexpr (sizeof(T) == 8) {
+      double d0, d1;
+      box_muller_f64(wr, wa, d0, d1);
+      c = (T)(d0 * (double)scale);
+      sn = (T)(d1 * (double)scale);
+    } else {
+      box_muller_f32(wr, wa, (float)scale, c, sn);
+    }
+    z[0] = (j0 & 1u) ? sn : c;
+    if constexpr (D == 2) z[1] = sn;
+  } else {
 #pragma unroll
   for (int blk = 0; blk < (D + 3) / 4; ++blk) {
     const uint4 w = philox4x32_10(noise_counter((uint32_t)p, (uint32_t)blk, tag, k), k0, k1);
@@ -51,6 +70,7 @@ __device__ __forceinline__ void spin_normals(uint64_t seed, uint32_t tag, uint64
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if (4 * blk + j < D) z[4 * blk + j] = zz[j];
+  }
   }
 }
 

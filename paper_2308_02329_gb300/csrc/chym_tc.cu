@@ -472,7 +472,8 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
             for (int mu = 0; mu < D; ++mu)
               tmem_ld2_wait<CH>(t_lane + acc_col + (uint32_t)(mu * RG + r0),
                                 t_lane + mst_col + (uint32_t)(mu * RG + r0), y[mu], x[mu]);
-            if (live) {
+            // D = 2: every lane takes part in the noise (lanes exchange normals)
+            if (live || D == 2) {
 #pragma unroll
               for (int j = 0; j < CH; j += 2) {  // two runs at once, FP32x2 arithmetic
                 const int r = r0 + j;
@@ -493,15 +494,41 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
                 }
                 const float2 e0 = make_float2(d.edt, d.edt), e1 = make_float2(d.edt * rA, d.edt * rB);
                 float2 z[4 * ((D + 3) / 4)];
+                if constexpr (D == 2) {
+                  // spins p and p ^ 1 share one Philox block per run (pair 0: the even
+                  // spin, pair 1: the odd one): each lane draws the block of one of the
+                  // two runs and hands the partner spin's pair to the partner lane
+                  const bool odd = (p & 1) != 0;
+                  const uint4 w = philox_rk(noise_counter((uint32_t)p >> 1, 0u, 0u, (uint64_t)(odd ? klB : klA)),
+                                            s_rk[g][odd ? r + 1 : r]);
+                  float2 zc, zs;
+                  box_muller_x2(w.x, w.y, w.z, w.w, neg2ln2s2, zc, zs);
+                  const float kc = odd ? zc.y : zc.x, ks = odd ? zs.y : zs.x;  // own spin, own run
+                  const float rc = __shfl_xor_sync(0xffffffffu, odd ? zc.x : zc.y, 1);
+                  const float rs = __shfl_xor_sync(0xffffffffu, odd ? zs.x : zs.y, 1);  // own spin, other run
+                  z[0] = odd ? make_float2(rc, kc) : make_float2(kc, rc);
+                  z[1] = odd ? make_float2(rs, ks) : make_float2(ks, rs);
+                  if (!live) continue;
+                } else if constexpr (D == 1) {
+                  // four spins share one block: spin p takes normal p % 4 of it
+                  const uint32_t j0 = (uint32_t)p & 3u;
+                  const uint4 wA = philox_rk(noise_counter((uint32_t)p >> 2, 0u, 0u, (uint64_t)klA), s_rk[g][r]);
+                  const uint4 wB = philox_rk(noise_counter((uint32_t)p >> 2, 0u, 0u, (uint64_t)klB), s_rk[g][r + 1]);
+                  float2 zc, zs;
+                  if (j0 >= 2u) box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, zc, zs);
+                  else box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, zc, zs);
+                  z[0] = (j0 & 1u) ? zs : zc;
+                } else {
 #pragma unroll
-                for (int blk = 0; blk < (D + 3) / 4; ++blk) {
-                  const uint4 wA = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)klA),
-                                             s_rk[g][r]);
-                  const uint4 wB = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)klB),
-                                             s_rk[g][r + 1]);
-                  box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, z[4 * blk], z[4 * blk + 1]);
-                  if (D - 4 * blk > 2)
-                    box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, z[4 * blk + 2], z[4 * blk + 3]);
+                  for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+                    const uint4 wA = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)klA),
+                                               s_rk[g][r]);
+                    const uint4 wB = philox_rk(noise_counter((uint32_t)p, (uint32_t)blk, 0u, (uint64_t)klB),
+                                               s_rk[g][r + 1]);
+                    box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, z[4 * blk], z[4 * blk + 1]);
+                    if (D - 4 * blk > 2)
+                      box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, z[4 * blk + 2], z[4 * blk + 3]);
+                  }
                 }
                 float2 xx[D], n2 = make_float2(0.f, 0.f);
 #pragma unroll

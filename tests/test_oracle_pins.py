@@ -58,10 +58,36 @@ def test_normals_distinct_streams():
     assert not np.allclose(a, O.normals(2, 0, 0, 64, 4))
     assert len(np.unique(a)) == a.size
     # steps beyond 2^32 use the high counter word
-    assert O.normal(5, 0, 1 << 32, 0, 0) != O.normal(5, 0, 0, 0, 0)
+    assert O.normal(5, 0, 1 << 32, 0, 0, 4) != O.normal(5, 0, 0, 0, 0, 4)
     # component mu and mu + 4 come from different Philox blocks
     b = O.normals(1, 0, 0, 16, 8)
     assert not np.allclose(b[:, :4], b[:, 4:])
+
+
+def test_normals_block_layout():
+    """One Philox block gives four normals: for D >= 3 they belong to one spin
+    (components mu = 4 b .. 4 b + 3), for D <= 2 to the 4/D spins that share the
+    block, in the order of the element index p D + mu, so that every word is used."""
+    def box_muller(w):
+        u = (np.asarray(w, dtype=np.float64) + 0.5) / 2.0 ** 32
+        r0, r1 = np.sqrt(-2 * np.log(u[0])), np.sqrt(-2 * np.log(u[2]))
+        t0, t1 = 2 * np.pi * u[1], 2 * np.pi * u[3]
+        return [r0 * np.cos(t0), r0 * np.sin(t0), r1 * np.cos(t1), r1 * np.sin(t1)]
+    seed, k = 0x1234567890ABCDEF, 41
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for D in (1, 2, 3, 4, 6):
+        z = O.normals(seed, 0, k, 12, D)
+        for p in range(12):
+            for mu in range(D):
+                if D <= 2:
+                    per = 4 // D
+                    ctr, j = [p // per, 0, k, 0], (p % per) * D + mu
+                else:
+                    ctr, j = [p, mu // 4, k, 0], mu % 4
+                zz = box_muller(O.philox4x32_10(ctr, key))[j]
+                assert abs(z[p, mu] - zz) <= 1e-12 * max(1.0, abs(zz))
+    # the initial state uses tag 1 in the same layout
+    assert O.normals(seed, 1, 0, 4, 2)[1, 0] != O.normals(seed, 0, 0, 4, 2)[1, 0]
 
 
 # --------------------------------------------------------------------------
