@@ -430,6 +430,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the planner's default cost model instead of measuring it")
     ap.add_argument("--learned-chunks", type=int, default=30,
                     help="chunks of 10 %% of the schedule in the learned leg's timed window "
                          "(after 10 uncounted burn-in chunks)")
@@ -516,7 +518,7 @@ def main():
         j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), j["n_h"], j["d_seeds"].data_ptr(),
                             j["runs"], 0, j["sched"], stream.cuda_stream)
     tuning = None
-    if prec == chym.PREC_BF16X2:
+    if prec == chym.PREC_BF16X2 and not args.no_tune:
         tuning = batch.tune([j["prm"] for j in jobs], [j["sched"] for j in jobs],
                             probe_steps=min(256, sim_steps), stream=stream.cuda_stream)
 

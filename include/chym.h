@@ -240,9 +240,11 @@ CHYM_API chym_status chym_batch_status(chym_batch* b);
  * (8 runs for D <= 4, 4 above) advanced one step on the small-N path; and one
  * unit of the large-N path (a 128-row output tile x one 64-wide K chunk) advanced
  * one step.  chym_batch_tune measures these costs on the current device for the
- * batch's own contexts: each group (the small-N contexts of one D, and all
- * large-N contexts) is integrated alone on the whole GPU for probe_steps steps,
- * once to warm up and once timed with CUDA events.  Every context's state, step
+ * batch's own contexts at the split they run with: the whole batch is integrated
+ * for probe_steps steps (once to warm up, then a few rounds timed per part with CUDA
+ * events); after each round every part's cost is re-estimated from its measured
+ * time and CTA count, which moves the next split towards equal finish times, and
+ * the split whose slowest part was fastest is kept.  Every context's state, step
  * and energies are restored afterwards, so tuning does not change any result.
  * Synchronous; needs the contexts' states (ESTATE otherwise); probe_steps >= 1. */
 CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,

@@ -40,6 +40,13 @@ struct chym_batch {
   double chunk_cost[9] = {0, 1.10, 0.64, 0.91, 1.01, 1.27, 1.43, 1.60, 1.76};
   double k2_cost = 1.05;
   bool tuned = false;
+  // Timing of the parts of a run (used by the tuner): index D = 1..8 for the small-N
+  // launch of dimension D, 0 for the large-N launches; their CTAs and work units.
+  bool timing = false;
+  cudaEvent_t t_begin[9] = {}, t_end[9] = {};
+  bool timed[9] = {};
+  int part_ctas[9] = {};
+  double part_units[9] = {};
 };
 
 namespace chym {
@@ -131,6 +138,10 @@ CHYM_API chym_status chym_batch_destroy(chym_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_plan) cudaFree(b->d_plan);
   if (b->d_status) cudaFree(b->d_status);
+  for (int p = 0; p <= 8; ++p) {
+    if (b->t_begin[p]) cudaEventDestroy(b->t_begin[p]);
+    if (b->t_end[p]) cudaEventDestroy(b->t_end[p]);
+  }
   k2_runner_release(b->k2);
   delete b;
   return CHYM_OK;
@@ -232,6 +243,9 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     std::vector<int> cta;
     plan_dimension(jobs, tc_chunk_runs(D), tc_runs_per_item(D), P, items, cta);
     DimLaunch L{D, (int)cta.size() - 1, kp_max, terms_max, 0, 0};
+    b->part_ctas[D] = L.P;
+    b->part_units[D] = 0.0;
+    for (const auto& jj : jobs) b->part_units[D] += (double)((jj.n_runs + tc_chunk_runs(D) - 1) / tc_chunk_runs(D));
     blob.resize((blob.size() + 15) / 16 * 16);
     L.items_off = blob.size();
     blob.insert(blob.end(), items.begin(), items.end());
@@ -255,11 +269,17 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   std::vector<bool> used(n, false);
   int si = 0;
   const unsigned char* base = (const unsigned char*)b->d_plan;
+  for (int D = 0; D <= 8; ++D) b->timed[D] = false;
   for (const auto& L : dl) {
     cudaStream_t s = b->streams[si];
     CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
+    if (b->timing) CHYM_CUDA_TRY(cudaEventRecord(b->t_begin[L.D], s));
     CHYM_CUDA_TRY(launch_tc_items(L.D, base, base + L.items_off, (const int*)(base + L.cta_off), L.P,
                                   steps, L.kp_max, L.terms_max, b->d_status, s));
+    if (b->timing) {
+      CHYM_CUDA_TRY(cudaEventRecord(b->t_end[L.D], s));
+      b->timed[L.D] = true;
+    }
     CHYM_CUDA_TRY(cudaEventRecord(b->joins[si], s));
     used[si++] = true;
   }
@@ -283,7 +303,19 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
       idx.push_back(i);
     }
     if (!idx.empty()) {
-      cudaError_t e = k2_integrate(b->k2, descs, dims, steps, b->d_status, s);
+      // the persistent large-N grid takes the SMs the small-N CTAs leave free
+      int small_ctas = 0;
+      for (const auto& L : dl) small_ctas += L.P;
+      const int cap = small_ctas > 0 ? std::max(1, b->sms - small_ctas) : 0;
+      b->part_ctas[0] = cap > 0 ? cap : b->sms;
+      b->part_units[0] = 0.0;
+      for (int i : idx) b->part_units[0] += (double)k2_work_units(b->ctxs[i]->N, b->ctxs[i]->D, b->ctxs[i]->n_runs);
+      if (b->timing) CHYM_CUDA_TRY(cudaEventRecord(b->t_begin[0], s));
+      cudaError_t e = k2_integrate(b->k2, descs, dims, steps, b->d_status, s, cap);
+      if (b->timing && e == cudaSuccess) {
+        CHYM_CUDA_TRY(cudaEventRecord(b->t_end[0], s));
+        b->timed[0] = true;
+      }
       if (e != cudaSuccess) return cuda_fail(e, "large-N batched integration");
       for (size_t t = 0; t < idx.size(); ++t) {
         chym_ctx* c = b->ctxs[idx[t]];
@@ -325,11 +357,13 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   return CHYM_OK;
 }
 
-// Autotuner: measure the planner's cost model on this device for the batch's own
-// contexts.  Each group (the small-N contexts of one dimension D; all large-N
-// contexts) is integrated alone on the whole GPU for probe_steps steps, once to
-// warm up (first launches, graph capture) and once timed with CUDA events; the
-// states, steps and energies of the contexts are saved before and restored after.
+// Autotuner: measure the planner's cost model on this device, for the batch's own
+// contexts and at the split it will run with.  The whole batch runs for probe_steps
+// steps (once untimed to warm up, then a few times timed per part with CUDA events);
+// after each timed run every part's cost is re-estimated from its measured time at
+// its CTA count (SM-microseconds per unit of work), which moves the next split
+// towards equal finish times.  The split with the shortest slowest part is kept.
+// The states, steps and energies of the contexts are saved before and restored after.
 CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
                                      const chym_schedule* schedules, int64_t probe_steps,
                                      void* cuda_stream) {
@@ -339,14 +373,6 @@ CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
   for (int i = 0; i < n; ++i)
     if (b->ctxs[i]->prec < 0) return fail(CHYM_ESTATE, "every context needs a state (chym_run with seeds first)");
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  // groups: 1..8 small-N dimensions, 0 the large-N contexts
-  std::vector<int> groups[9];
-  for (int i = 0; i < n; ++i) {
-    const chym_ctx* c = b->ctxs[i];
-    if (params[i].prec != CHYM_PREC_BF16X2) continue;
-    groups[c->N <= 128 ? c->D : 0].push_back(i);
-  }
-  // save the states of every context that takes part
   struct Saved {
     void* d = nullptr;
     size_t bytes = 0;
@@ -358,86 +384,83 @@ CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
     for (auto& sv : saved)
       if (sv.d) cudaFree(sv.d);
   };
-  for (int g = 0; g <= 8; ++g)
-    for (int i : groups[g]) {
-      chym_ctx* c = b->ctxs[i];
-      Saved& sv = saved[i];
-      sv.bytes = (size_t)c->n_runs * c->N * c->D * (c->prec == CHYM_PREC_FP64 ? 8 : 4);
-      sv.k = c->k;
-      sv.have_energy = c->have_energy;
-      cudaError_t e = cudaMalloc(&sv.d, sv.bytes);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(sv.d, c->d_X, sv.bytes, cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess) {
-        release();
-        return cuda_fail(e, "chym_batch_tune: state snapshot");
-      }
-    }
-  cudaEvent_t t0 = nullptr, t1 = nullptr;
-  chym_status status = CHYM_OK;
-  cudaError_t e = cudaEventCreate(&t0);
-  if (e == cudaSuccess) e = cudaEventCreate(&t1);
-  if (e != cudaSuccess) status = cuda_fail(e, "chym_batch_tune: events");
-  double new_chunk[9];
-  for (int D = 0; D <= 8; ++D) new_chunk[D] = b->chunk_cost[D];
-  double new_k2 = b->k2_cost;
-  for (int g = 0; g <= 8 && status == CHYM_OK; ++g) {
-    if (groups[g].empty()) continue;
-    std::vector<chym_ctx*> cs;
-    std::vector<chym_params> ps;
-    std::vector<chym_schedule> ss;
-    for (int i : groups[g]) {
-      cs.push_back(b->ctxs[i]);
-      ps.push_back(params[i]);
-      ss.push_back(schedules[i]);
-    }
-    chym_batch* sub = nullptr;
-    status = chym_batch_create(cs.data(), (int)cs.size(), &sub);
-    if (status != CHYM_OK) break;
-    float ms = 0.f;
-    status = chym_batch_run(sub, ps.data(), ss.data(), probe_steps, st);
-    if (status == CHYM_OK) {
-      e = cudaEventRecord(t0, st);
-      if (e == cudaSuccess) status = chym_batch_run(sub, ps.data(), ss.data(), probe_steps, st);
-      if (e == cudaSuccess && status == CHYM_OK) e = cudaEventRecord(t1, st);
-      if (e == cudaSuccess && status == CHYM_OK) e = cudaEventSynchronize(t1);
-      if (e == cudaSuccess && status == CHYM_OK) e = cudaEventElapsedTime(&ms, t0, t1);
-      if (e != cudaSuccess && status == CHYM_OK) status = cuda_fail(e, "chym_batch_tune: timing");
-    }
-    if (status == CHYM_OK) status = chym_batch_status(sub);
-    chym_batch_destroy(sub);
-    if (status != CHYM_OK) break;
-    const double us = 1e3 * (double)ms;
-    if (g > 0) {
-      long long C = 0;
-      for (chym_ctx* c : cs) C += (c->n_runs + tc_chunk_runs(g) - 1) / tc_chunk_runs(g);
-      const long long P = std::min<long long>(b->sms, C);
-      const long long per_cta = (C + P - 1) / P;
-      new_chunk[g] = us / ((double)per_cta * (double)probe_steps);
-    } else {
-      long long U = 0;
-      for (chym_ctx* c : cs) U += k2_work_units(c->N, c->D, c->n_runs);
-      new_k2 = us * (double)b->sms / ((double)U * (double)probe_steps);
+  for (int i = 0; i < n; ++i) {
+    chym_ctx* c = b->ctxs[i];
+    Saved& sv = saved[i];
+    sv.bytes = (size_t)c->n_runs * c->N * c->D * (c->prec == CHYM_PREC_FP64 ? 8 : 4);
+    sv.k = c->k;
+    sv.have_energy = c->have_energy;
+    cudaError_t e = cudaMalloc(&sv.d, sv.bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv.d, c->d_X, sv.bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(e, "chym_batch_tune: state snapshot");
     }
   }
-  // restore the states
-  for (int g = 0; g <= 8; ++g)
-    for (int i : groups[g]) {
-      chym_ctx* c = b->ctxs[i];
-      const Saved& sv = saved[i];
-      if (!sv.d) continue;
-      e = cudaMemcpyAsync(c->d_X, sv.d, sv.bytes, cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess && status == CHYM_OK) status = cuda_fail(e, "chym_batch_tune: state restore");
-      c->k = sv.k;
-      c->have_energy = sv.have_energy;
+  chym_status status = CHYM_OK;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p <= 8 && e == cudaSuccess; ++p) {
+    if (!b->t_begin[p]) e = cudaEventCreate(&b->t_begin[p]);
+    if (e == cudaSuccess && !b->t_end[p]) e = cudaEventCreate(&b->t_end[p]);
+  }
+  if (e != cudaSuccess) status = cuda_fail(e, "chym_batch_tune: events");
+  double best_chunk[9], best_k2 = b->k2_cost, best_T = INFINITY;
+  for (int D = 0; D <= 8; ++D) best_chunk[D] = b->chunk_cost[D];
+  constexpr int kRounds = 4;
+  for (int round = -1; round < kRounds && status == CHYM_OK; ++round) {
+    b->timing = round >= 0;
+    status = chym_batch_run(b, params, schedules, probe_steps, st);
+    if (status != CHYM_OK) break;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      status = cuda_fail(e, "chym_batch_tune: probe");
+      break;
     }
+    status = chym_batch_status(b);
+    if (status != CHYM_OK || round < 0) continue;
+    double T_max = 0.0, T[9] = {0};
+    for (int p = 0; p <= 8; ++p) {
+      if (!b->timed[p]) continue;
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, b->t_begin[p], b->t_end[p]);
+      if (e != cudaSuccess) break;
+      T[p] = 1e3 * (double)ms;
+      T_max = std::max(T_max, T[p]);
+    }
+    if (e != cudaSuccess) {
+      status = cuda_fail(e, "chym_batch_tune: timing");
+      break;
+    }
+    if (T_max < best_T) {  // the split of this round is the best so far
+      best_T = T_max;
+      for (int D = 0; D <= 8; ++D) best_chunk[D] = b->chunk_cost[D];
+      best_k2 = b->k2_cost;
+    }
+    // re-estimate each part's cost at its operating point
+    for (int p = 0; p <= 8; ++p) {
+      if (!b->timed[p] || b->part_units[p] <= 0.0 || T[p] <= 0.0) continue;
+      const double c = T[p] * (double)b->part_ctas[p] / (b->part_units[p] * (double)probe_steps);
+      if (p == 0) b->k2_cost = c;
+      else b->chunk_cost[p] = c;
+    }
+  }
+  b->timing = false;
+  // restore the states
+  for (int i = 0; i < n; ++i) {
+    chym_ctx* c = b->ctxs[i];
+    const Saved& sv = saved[i];
+    if (!sv.d) continue;
+    e = cudaMemcpyAsync(c->d_X, sv.d, sv.bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess && status == CHYM_OK) status = cuda_fail(e, "chym_batch_tune: state restore");
+    c->k = sv.k;
+    c->have_energy = sv.have_energy;
+  }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess && status == CHYM_OK) status = cuda_fail(e, "chym_batch_tune");
   release();
-  if (t0) cudaEventDestroy(t0);
-  if (t1) cudaEventDestroy(t1);
+  for (int D = 0; D <= 8; ++D) b->chunk_cost[D] = best_chunk[D];
+  b->k2_cost = best_k2;
   if (status != CHYM_OK) return status;
-  for (int D = 0; D <= 8; ++D) b->chunk_cost[D] = new_chunk[D];
-  b->k2_cost = new_k2;
   b->tuned = true;
   return CHYM_OK;
 }

@@ -130,6 +130,7 @@ struct K2Runner {
   size_t sig_tiles = 0;
   std::vector<int> sig_dims;
   void* sig_buf = nullptr;
+  int sig_cap = 0;
   int sms = 0;
 };
 }  // namespace chym
@@ -185,14 +186,17 @@ size_t k2_desc_bytes();
 // tiles x K chunks of one step of a large-N context (the planner's work unit)
 long long k2_work_units(int N, int D, int n_runs);
 cudaError_t k2_finish(chym_ctx* c, const void* desc, cudaStream_t st);
+// max_ctas > 0 caps the persistent grid (the SMs left to the large-N path when the
+// small-N kernels of a batch occupy the others).
 cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
                          const std::vector<int>& dims, int64_t steps, unsigned* status,
-                         cudaStream_t st);
+                         cudaStream_t st, int max_ctas = 0);
 void k2_runner_release(K2Runner& R);
 // small-N tensor-core kernel over an item plan (chym_tc.cu)
 cudaError_t prepare_tc_operand(chym_ctx* c);
 int tc_runs_per_item(int D);
 int tc_chunk_runs(int D);
+int tc_groups(int D);  // warpgroups of a CTA: the chunks it advances side by side
 size_t tc_desc_bytes();
 size_t tc_item_bytes();
 void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out);

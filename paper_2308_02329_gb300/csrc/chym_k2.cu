@@ -741,7 +741,7 @@ cudaError_t k2_finish(chym_ctx* c, const void* desc, cudaStream_t st) {
 // replayed.
 cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
                          const std::vector<int>& dims, int64_t steps, unsigned* status,
-                         cudaStream_t st) {
+                         cudaStream_t st, int max_ctas) {
   const size_t db = sizeof(K2Desc);
   const int n_desc = (int)dims.size();
   cudaError_t e = cudaSuccess;
@@ -799,7 +799,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
           (int)std::min<size_t>(kMaxStages, std::max<size_t>(2, kRingBudget / dim_stride[D]));
       // at least 120 KB: one CTA (which owns 512 TMEM columns) per SM
       const size_t smem = std::max<size_t>((size_t)stages * dim_stride[D], 120 * 1024);
-      const int grid = std::min(dim_count[D], R.sms);
+      const int grid = std::min(dim_count[D], max_ctas > 0 ? std::min(max_ctas, R.sms) : R.sms);
       K2Launch L{d_descs, d_tiles + dim_first[D], d_done, dim_count[D], k_off, stages, dim_stride[D],
                  status};
       cudaError_t r = k2_launch(D, L, grid, smem, s);
@@ -812,7 +812,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
     // the graph stays valid while the tile table keeps its shape; the descriptor
     // contents are refreshed in place above
     const bool reuse = R.exec && R.sig_tiles == tiles.size() && R.sig_dims == dim_count &&
-                       R.sig_buf == R.d_buf;
+                       R.sig_buf == R.d_buf && R.sig_cap == max_ctas;
     if (!reuse) {
       if (R.exec) cudaGraphExecDestroy(R.exec);
       R.exec = nullptr;
@@ -832,6 +832,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
       R.sig_tiles = tiles.size();
       R.sig_dims = dim_count;
       R.sig_buf = R.d_buf;
+      R.sig_cap = max_ctas;
     }
     for (int64_t c = 0; c < chunks; ++c) {
       e = cudaGraphLaunch(R.exec, st);

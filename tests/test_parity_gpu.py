@@ -355,6 +355,8 @@ K2_CASES = [
     (190, 6, 1, 17, 20, "sk"),
     (133, 7, 1, 17, 20, "sparse"),
     (1000, 4, 2, 3, 15, "sk"),
+    (2000, 8, 1, 3, 6, "sk"),       # the largest instances of the uneven workload
+    (4096, 2, 1, 2, 4, "sk"),       # the largest N the features and tiles are sized for
 ]
 
 
