@@ -227,6 +227,59 @@ double oracle_ising_energy(const double* J, int N, const int8_t* s) {
   return -e;
 }
 
+/* Best-axis rounding of a two-component (XY, D = 2) state: among all axes     */
+/* u = (cos phi, sin phi), the Ising pattern s_p = +1 if x_p . u >= 0 else -1 */
+/* with the lowest energy E = -sum J s s.  The pattern changes only where an  */
+/* axis is perpendicular to a spin, at phi_p = theta_p + pi/2 (mod pi), so the */
+/* candidates are one axis inside every interval between consecutive distinct */
+/* critical angles (phi and phi + pi give opposite patterns of equal energy). */
+/* Spins of zero length project to 0 and stay +1.  Written plainly: every     */
+/* candidate's pattern and energy from scratch, O(N^3).  Returns the lowest   */
+/* energy and the first pattern (in increasing phi) that reaches it.          */
+/* ------------------------------------------------------------------------ */
+static int cmp_double(const void* a, const void* b) {
+  const double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+double oracle_round_xy(const double* J, int N, const double* x, int8_t* s_out) {
+  const double pi = 3.14159265358979323846;
+  double* crit = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+  int8_t* s = (int8_t*)malloc((size_t)(N > 0 ? N : 1));
+  int n_crit = 0;
+  for (int p = 0; p < N; ++p) {
+    const double a = x[2 * (size_t)p], b = x[2 * (size_t)p + 1];
+    if (a == 0.0 && b == 0.0) continue;
+    double c = fmod(atan2(b, a) + 0.5 * pi, pi);
+    if (c < 0.0) c += pi;
+    crit[n_crit++] = c;
+  }
+  qsort(crit, (size_t)n_crit, sizeof(double), cmp_double);
+  int n_dist = 0;
+  for (int i = 0; i < n_crit; ++i)
+    if (n_dist == 0 || crit[i] != crit[n_dist - 1]) crit[n_dist++] = crit[i];
+  double best = INFINITY;
+  const int n_cand = n_dist > 0 ? n_dist : 1;
+  for (int i = 0; i < n_cand; ++i) {
+    /* the interval after critical angle i (the last one wraps around through pi) */
+    double phi;
+    if (n_dist == 0) phi = 0.0;
+    else if (i + 1 < n_dist) phi = 0.5 * (crit[i] + crit[i + 1]);
+    else phi = 0.5 * (crit[i] + crit[0] + pi);
+    const double u0 = cos(phi), u1 = sin(phi);
+    for (int p = 0; p < N; ++p)
+      s[p] = (x[2 * (size_t)p] * u0 + x[2 * (size_t)p + 1] * u1 >= 0.0) ? 1 : -1;
+    const double e = oracle_ising_energy(J, N, s);
+    if (e < best) {
+      best = e;
+      if (s_out) memcpy(s_out, s, (size_t)N);
+    }
+  }
+  free(crit);
+  free(s);
+  return best;
+}
+
 /* Hyperspin energy of Eq. 3 with sigma_p = x_p / |x_p| (zero vector if      */
 /* x_p = 0).                                                                 */
 double oracle_hyperspin_energy(const double* J, int N, int D, const double* x) {

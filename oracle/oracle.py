@@ -26,6 +26,8 @@ def _L():
         lib.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
         lib.oracle_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+        lib.oracle_round_xy.argtypes = [dp, ctypes.c_int, dp, i8p]
+        lib.oracle_round_xy.restype = ctypes.c_double
         lib.oracle_normal.restype = ctypes.c_double
         lib.oracle_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                        ctypes.c_int, ctypes.c_int, dp]
@@ -168,6 +170,16 @@ def ising_energy(J, s):
 
 def ising_energies(J, S):
     return np.array([ising_energy(J, s) for s in S], dtype=np.float64)
+
+
+def round_xy(J, x):
+    """Best-axis rounding of one D = 2 state x (N x 2): (energy, spins)."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    s = np.zeros(x.shape[0], dtype=np.int8)
+    e = _L().oracle_round_xy(_p(J, ctypes.c_double), J.shape[0], _p(x, ctypes.c_double),
+                             _p(s, ctypes.c_int8))
+    return e, s
 
 
 def hyperspin_energy(J, x):

@@ -341,3 +341,55 @@ def test_figures_of_merit_hand_example():
     lv, ct = energy_histogram(E)
     assert lv.tolist() == [-12, -8, -4] and ct.tolist() == [5, 6, 1]
     assert hits_per_h([-1.0 + 1e-12, np.nan], -1.0, 2, real_j=True).tolist() == [1, 0]
+
+
+# --------------------------------------------------------------------------
+# Best-axis rounding of XY states (D = 2)
+# --------------------------------------------------------------------------
+def _grid_round_xy(J, x, n_phi):
+    """The lowest Ising energy of the patterns sign(x . u(phi)) over a uniform grid of
+    n_phi axes in [0, pi): a brute force that knows nothing of critical angles."""
+    best = np.inf
+    for phi in (np.arange(n_phi) + 0.5) * np.pi / n_phi:
+        s = np.where(x @ np.array([np.cos(phi), np.sin(phi)]) >= 0, 1, -1).astype(np.int8)
+        best = min(best, O.ising_energy(J, s))
+    return best
+
+
+def test_round_xy_matches_a_fine_grid_of_axes():
+    for seed in range(6):
+        rng = np.random.default_rng(seed)
+        N = 9
+        J = inputs.sk_pm1(N, 100 + seed)
+        x = rng.standard_normal((N, 2))
+        crit = np.sort(np.mod(np.arctan2(x[:, 1], x[:, 0]) + np.pi / 2, np.pi))
+        gaps = np.diff(np.concatenate([crit, [crit[0] + np.pi]]))
+        n_phi = 20000
+        assert gaps.min() > 2 * np.pi / n_phi    # every pattern interval holds grid points
+        e, s = O.round_xy(J, x)
+        assert e == _grid_round_xy(J, x, n_phi)
+        assert O.ising_energy(J, s) == e
+
+
+def test_round_xy_invariances():
+    rng = np.random.default_rng(3)
+    N = 14
+    J = inputs.sk_pm1(N, 5)
+    x = rng.standard_normal((N, 2))
+    e, _ = O.round_xy(J, x)
+    # never worse than reading the first component (the axis phi = 0 is a candidate)
+    assert e <= O.ising_energy(J, np.where(x[:, 0] >= 0, 1, -1).astype(np.int8))
+    # a common rotation of every spin leaves the best axis energy unchanged
+    for psi in (0.3, 1.1, 2.9):
+        R = np.array([[np.cos(psi), -np.sin(psi)], [np.sin(psi), np.cos(psi)]])
+        assert O.round_xy(J, x @ R.T)[0] == e
+    # spins already on the first axis: the plain readout is the best pattern (or its flip)
+    y = np.stack([np.sign(x[:, 0]) * (1 + rng.random(N)), np.zeros(N)], axis=1)
+    e1, s1 = O.round_xy(J, y)
+    assert e1 == O.ising_energy(J, np.where(y[:, 0] >= 0, 1, -1).astype(np.int8))
+    assert abs(int(s1 @ np.sign(y[:, 0]))) == N
+    # a spin of zero length projects to zero and reads +1 on every axis
+    z = x.copy()
+    z[4] = 0.0
+    ez, sz = O.round_xy(J, z)
+    assert sz[4] == 1 and O.ising_energy(J, sz) == ez
