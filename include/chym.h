@@ -146,6 +146,22 @@ CHYM_API chym_status chym_energy(chym_ctx* ctx, double* E_out, uint64_t* spins_o
  * d_spins are device pointers; asynchronous. */
 CHYM_API chym_status chym_energy_device(chym_ctx* ctx, double* d_E, uint64_t* d_spins, void* cuda_stream);
 
+/* Readout of XY runs (D = 2, the XY machine of the text after Fig. 2) by
+ * best-axis rounding: instead of the first component, the Ising pattern
+ * s_p = sign(x_p . u) along the axis u = (cos phi, sin phi) whose pattern has the
+ * lowest energy E = -sum_{p,q} J_pq s_p s_q, over all axes (the pattern changes
+ * only where u is perpendicular to a spin; phi and phi + pi give opposite patterns
+ * of equal energy).  A spin of zero length reads +1.  Same outputs and layouts as
+ * chym_energy; the lowest energy is unique, its pattern is the first reached when
+ * the axis turns from inside the interval that wraps through pi.  EINVAL unless
+ * D = 2 and N <= 4096; ESTATE without a state.  chym_readout_xy writes into the
+ * context's energy buffers (the cached Ising energies of chym_energy are dropped)
+ * and synchronises the stream; the device variant writes d_E (n_runs doubles)
+ * and nullable d_spins and is asynchronous. */
+CHYM_API chym_status chym_readout_xy(chym_ctx* ctx, double* E_out, uint64_t* spins_out, void* cuda_stream);
+CHYM_API chym_status chym_readout_xy_device(chym_ctx* ctx, double* d_E, uint64_t* d_spins,
+                                            void* cuda_stream);
+
 /* Ground-state statistics of the last energies (figures of merit (i)-(iii)
  * after Fig. 3): hits_per_h (nullable, n_h int64) counts replicas with
  * E == E_gs (|E - E_gs| <= 1e-9 |E_gs| for real J); hist (nullable, n_bins

@@ -22,7 +22,8 @@ PREC_FP64, PREC_FP32, PREC_BF16X2 = 0, 1, 2
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP", 6: "ESTATE"}
 
 EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", "chym_run",
-           "chym_run_device", "chym_energy", "chym_energy_device", "chym_stats",
+           "chym_run_device", "chym_energy", "chym_energy_device", "chym_readout_xy",
+           "chym_readout_xy_device", "chym_stats",
            "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
            "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
            "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
@@ -106,6 +107,8 @@ def lib():
         L.chym_run_device.argtypes = L.chym_run.argtypes
         L.chym_energy.argtypes = [vp, vp, vp, vp]
         L.chym_energy_device.argtypes = [vp, vp, vp, vp]
+        L.chym_readout_xy.argtypes = [vp, vp, vp, vp]
+        L.chym_readout_xy_device.argtypes = [vp, vp, vp, vp]
         L.chym_stats.argtypes = [vp, dbl, ctypes.POINTER(CStats), vp, vp, i32, vp]
         L.chym_get_state.argtypes = [vp, vp, ctypes.POINTER(i64), vp]
         L.chym_set_state.argtypes = [vp, vp, i32, vp, i32, vp, i64, ctypes.c_int32, vp]
@@ -212,6 +215,18 @@ class Context:
     def energy_device(self, d_E, d_spins=0, stream=0):
         _check(lib().chym_energy_device(self._h, ctypes.c_void_p(d_E), ctypes.c_void_p(d_spins),
                                         ctypes.c_void_p(stream)))
+
+    def readout_xy(self, spins=False, stream=0):
+        """Best-axis rounding of D = 2 runs (chym_readout_xy): energies (and packed spins)."""
+        n_runs = self.info()[0]
+        E = np.zeros(n_runs, dtype=np.float64)
+        S = np.zeros((n_runs, (self.N + 63) // 64), dtype=np.uint64) if spins else None
+        _check(lib().chym_readout_xy(self._h, _ptr(E), _ptr(S), ctypes.c_void_p(stream)))
+        return (E, S) if spins else E
+
+    def readout_xy_device(self, d_E, d_spins=0, stream=0):
+        _check(lib().chym_readout_xy_device(self._h, ctypes.c_void_p(d_E), ctypes.c_void_p(d_spins),
+                                            ctypes.c_void_p(stream)))
 
     def stats(self, E_gs, n_bins=0, stream=0):
         n_runs, n_h, _ = self.info()

@@ -341,6 +341,46 @@ def test_bf16x2_statistical_parity_long_horizon():
 
 
 # ---------------------------------------------------------------------------
+# XY readout by best-axis rounding (D = 2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,graph,prec", [(30, "sk", chym.PREC_BF16X2), (100, "mobius", chym.PREC_BF16X2),
+                                          (150, "gauss", chym.PREC_BF16X2), (24, "sk", chym.PREC_FP64),
+                                          (45, "sparse", chym.PREC_FP32), (257, "sk", chym.PREC_BF16X2)])
+def test_readout_xy_matches_checker(N, graph, prec):
+    """XY machine (D = 2, no annealing): the best-axis energies equal the checker's
+    rounding of the same final states (exactly for +-1 couplings), the returned
+    spins reach them, and they are never above the first-component readout."""
+    J, eps, h, seeds = make_case(N, 2, 2, 8, 21, graph)
+    kind = chym.J_REAL if graph == "gauss" else chym.J_PM1
+    ctx = chym.Context(J, 2, kind)
+    prm = chym.Params(eps=eps, prec=prec, kappa=1e-3)
+    ctx.run(prm, h, seeds, 300, chym.Schedule(0, 0, 300))
+    X, _ = ctx.get_state()
+    E_plain = ctx.energy()
+    E, S = ctx.readout_xy(spins=True)
+    s = chym.unpack_spins(S, N)
+    for r in range(len(seeds)):
+        e_o, _ = O.round_xy(J, X[r].astype(np.float64))
+        if kind == chym.J_PM1:
+            assert E[r] == e_o
+            assert O.ising_energy(J, s[r]) == E[r]
+        else:
+            assert abs(E[r] - e_o) <= 1e-9 * max(1.0, abs(e_o))
+            assert abs(O.ising_energy(J, s[r]) - E[r]) <= 1e-9 * max(1.0, abs(E[r]))
+        assert E[r] <= E_plain[r] + 1e-9 * max(1.0, abs(E_plain[r]))
+    torch = pytest.importorskip("torch")
+    d_E = torch.empty(len(seeds), dtype=torch.float64, device="cuda")
+    ctx.readout_xy_device(d_E.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(d_E.cpu().numpy(), E)
+    ctx.close()
+    c3 = chym.Context(J, 3, kind)
+    with pytest.raises(chym.ChymError):
+        c3.readout_xy()
+    c3.close()
+
+
+# ---------------------------------------------------------------------------
 # large-N path (N > 128): per-step tcgen05 GEMM with the update in its epilogue
 # ---------------------------------------------------------------------------
 K2_CASES = [
