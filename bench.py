@@ -82,7 +82,13 @@ WORKLOADS = {
     "fig4": Workload("fig4", "size scaling of Fig. 4: 20 % sparse +-1 graphs, N = 10..100, 16 graphs "
                      "per N; CIM (D=1, 51 h) and CHYM+DA (D=2 annealed, 21 h), 32 replicas, "
                      "20000 steps dt=0.01", [], (1, 2), 21, 32, 20000, compare_plain=False),
+    "map": Workload("map", "SK+-1 N=100, D=3, the cavity round-trip map of Eq. 1-2 (a=0.95, d=0.1, "
+                    "beta=100), 32 gain values K = K_th (1 + dK), dK in [0, 0.25], 512 replicas "
+                    "each (16384 runs), 20000 round trips", [("sk", "sk", 100)], (3,), 32, 512, 20000,
+                    compare_plain=False),
 }
+MAP_CAVITY = {"a": 0.95, "d": 0.1, "beta": 100.0}
+MAP_GAIN_SPAN = 0.25
 FIG4_NS = tuple(range(10, 101, 10))
 FIG4_GRAPHS = 16
 UNEVEN_INSTANCES = 512
@@ -109,6 +115,14 @@ def workload_specs(w, rank):
                                 n_h=51 if m["D"] == 1 else 21, gamma=m["gamma"],
                                 mode=(m["kappa"], 1 if m["anneal"] else 0)))
                 out[-1]["mode"] = mode
+        return out
+    if w.key == "map":   # one context per gain value: eps and gamma follow the gain
+        out = []
+        for dk in np.linspace(0.0, MAP_GAIN_SPAN, w.n_h):
+            for name, kind, N in w.graphs:
+                for D in w.D:
+                    out.append(spec(name, kind, N, D, None, n_h=1, mode=(0.0, 0)))
+                    out[-1]["gain_rel"] = float(dk)
         return out
     return [spec(name, kind, N, D, None) for name, kind, N in w.graphs for D in w.D]
 
@@ -139,9 +153,23 @@ def workload_config(w, prec_name, sim_steps):
         graphs = [f"{FIG4_GRAPHS} sparse +-1 graphs (density 0.2) per N in {list(FIG4_NS)}"]
     else:
         graphs = [f"{UNEVEN_INSTANCES} SK+-1 instances, N in [50, 2000]"]
-    return {"workload": w.title, "key": w.key, "graphs": graphs, "D": list(w.D),
-            "runs_per_graph": w.runs, "n_h": w.n_h, "replicas": w.reps, "steps": sim_steps,
-            "precision": prec_name, "l2": "flushed between steps (256 MiB write)"}
+    cfg = {"workload": w.title, "key": w.key, "graphs": graphs, "D": list(w.D),
+           "runs_per_graph": w.runs, "n_h": w.n_h, "replicas": w.reps, "steps": sim_steps,
+           "precision": prec_name, "l2": "flushed between steps (256 MiB write)"}
+    if w.key == "map":
+        cfg["cavity"] = dict(MAP_CAVITY)
+        cfg["gains"] = f"K_th (1 + dK), dK = linspace(0, {MAP_GAIN_SPAN}, {w.n_h}), one context each"
+    return cfg
+
+
+def map_euler(lam, gain_rel):
+    """Euler form of one round trip (dt = 1) at gain K = K_th (1 + gain_rel): the
+    (dt, sigma, init_std, gamma, kappa, eps) tuple and the pump value h."""
+    a, d, beta = MAP_CAVITY["a"], MAP_CAVITY["d"], MAP_CAVITY["beta"]
+    b = 1.0 - a
+    K = (1.0 + gain_rel) / ((1.0 - d) * (a + b * lam))
+    g = (1.0 - d) * K
+    return (1.0, 1e-3, 0.1, g * b * b * beta * K * K, 0.0, g * b), g * a
 
 
 def measured_peaks():
@@ -249,6 +277,8 @@ def oracle_jobs(w):
     specs = workload_specs(w, 0)
     if w.key in ("uneven", "fig4"):
         specs = specs[::32]
+    elif w.key == "map":
+        specs = specs[::8]
     cache = {}
     for sp in specs:
         kind, N, seed = sp["kind"], sp["N"], sp["seed"]
@@ -257,9 +287,14 @@ def oracle_jobs(w):
             lam = float(np.linalg.eigvalsh(J)[-1])
             cache[(kind, N, seed)] = (J, lam if lam > 0 else 1.0)
         J, lam = cache[(kind, N, seed)]
+        if "gain_rel" in sp:
+            (dt, sg, i0, ga, ka, ep), h = map_euler(lam, sp["gain_rel"])
+            prm = O.Params(dt=dt, sigma=sg, init_std=i0, gamma=ga, kappa=ka, eps=ep)
+            jobs.append((J, sp["D"], prm, O.Schedule(0, 0, 0), h))
+            continue
         prm = O.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=sp["gamma"], kappa=sp["kappa"],
                        eps=EPS_HAT / lam)
-        jobs.append((J, sp["D"], prm, O.Schedule(sp["skind"], w.steps // 2, w.steps)))
+        jobs.append((J, sp["D"], prm, O.Schedule(sp["skind"], w.steps // 2, w.steps), None))
     return jobs
 
 
@@ -268,10 +303,10 @@ def time_oracle(jobs, runs, steps, threads):
     import oracle.oracle as O
     from paper_2308_02329_gb300 import inputs
     t0 = time.perf_counter()
-    for J, D, prm, sch in jobs:
+    for J, D, prm, sch, h_map in jobs:
         N = J.shape[0]
         seeds = inputs.run_seeds(INSTANCE_SEED, runs)
-        h = np.resize(inputs.pump_grid(1.0 - EPS_HAT, 8), runs)
+        h = np.resize(inputs.pump_grid(1.0 - EPS_HAT, 8), runs) if h_map is None else np.full(runs, h_map)
         X = O.init_state(N, D, seeds, prm.init_std)
         O.integrate(J, X, h, seeds, prm, sch, 0, steps, threads=threads)
         O.ising_energies(J, O.readout(X))
@@ -287,7 +322,7 @@ def cpu_baseline_sample(w, target_s=10.0):
     t = time_oracle(jobs, runs, probe, threads)
     steps = int(max(probe, min(w.steps, probe * target_s / max(t, 1e-6))))
     el = time_oracle(jobs, runs, steps, threads)
-    work = sum(J.shape[0] * D * runs * steps for J, D, _, _ in jobs)
+    work = sum(J.shape[0] * D * runs * steps for J, D, *_ in jobs)
     return {"value": work / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{len(jobs)} (graph, D) contexts of the workload, {runs} runs x {steps} of "
                       f"{w.steps} steps each, FP64, OpenMP over runs; {el:.1f} s"}
@@ -306,7 +341,7 @@ def run_reference(args, w, rank, world):
     for _ in range(args.warmup):
         time_oracle(jobs, runs, steps, threads)
     el = sum(time_oracle(jobs, runs, steps, threads) for _ in range(args.steps))
-    work = sum(J.shape[0] * D * runs * steps for J, D, _, _ in jobs)
+    work = sum(J.shape[0] * D * runs * steps for J, D, *_ in jobs)
     value = work * args.steps / el
     sample = (f"per step: {len(jobs)} (graph, D) contexts of the workload, {runs} runs x {steps} of {w.steps} "
               f"steps each, FP64, OpenMP over runs")
@@ -493,6 +528,7 @@ def main():
         sd = INSTANCE_SEED + 7919 * rank + 97 * gi + D if seed is None else seed + D
         seeds = inputs.run_seeds(sd, runs)
         jobs.append(dict(name=name, N=N, D=D, ctx=ctx, kappa=sp["kappa"], skind=sp["skind"],
+                         gain_rel=sp.get("gain_rel"),
                          gamma=sp["gamma"], mode=sp.get("mode"), n_h=n_h, runs=runs, h=h,
                          seeds=seeds, d_h=torch.from_numpy(h).to(dev),
                          d_seeds=torch.from_numpy(seeds.view(np.int64)).to(dev),
@@ -508,6 +544,11 @@ def main():
         j["prm"] = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=j["gamma"], kappa=j["kappa"],
                                eps=EPS_HAT / lam if lam > 0 else 0.0, prec=prec)
         j["sched"] = chym.Schedule(j["skind"], sim_steps // 2 if j["skind"] else 0, sim_steps)
+        if j["gain_rel"] is not None:   # the round-trip map: dt = 1, per-gain constants
+            (dt, sg, i0, ga, ka, ep), h = map_euler(lam, j["gain_rel"])
+            j["prm"] = chym.Params(dt=dt, sigma=sg, init_std=i0, gamma=ga, kappa=ka, eps=ep, prec=prec)
+            j["h"] = np.array([h])
+            j["d_h"] = torch.from_numpy(j["h"]).to(dev)
     graphs.clear()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     streams = [torch.cuda.Stream(dev) for _ in jobs]
