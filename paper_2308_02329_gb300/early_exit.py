@@ -147,83 +147,116 @@ def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, c
     run uncounted and untimed, so that the counted window starts from slots already
     spread over their schedules (and after first-call costs).  `theta` is one
     threshold or one per context.  With a `trace` list, every chunk appends (chunk,
-    context, decisions, retired, completed, hits)."""
+    context, decisions, retired, completed, hits).
+
+    The bookkeeping of a chunk stays on the device (local steps, energies, features,
+    logits, restart masks and their ordered indices) and meets the host once: one
+    copy of all counts, after which the fresh seeds and pump indices of the restarted
+    slots go up in one pinned copy and the reseeds are queued."""
+    import contextlib
     torch = _torch()
-    out = Outcome()
     n = len(ctxs)
     thetas = list(theta) if np.ndim(theta) else [theta] * n
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    per = []
-    for ctx, prm, sched, h, R, ss in zip(ctxs, prms, scheds, hs, Rs, seed_streams):
-        ctx.run(prm, h, ss.take(R), 0, sched, stream)
-        dt = torch.float64 if prm.prec == chym.PREC_FP64 else torch.float32
-        per.append(dict(
-            next_h=0, offs=torch.zeros(R, dtype=torch.int64, device="cuda"),
-            snap=torch.empty(ctx.N * ctx.D * R, dtype=dt, device="cuda"),
-            F=torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda"),
-            E=torch.empty(R, dtype=torch.float64, device="cuda")))
-
-    def advance(steps):
+    gated = [net is not None and th > -np.inf for th in thetas]
+    # the device-side bookkeeping runs on the library's stream
+    cur = torch.cuda.current_stream()
+    if stream == cur.cuda_stream:
+        on = contextlib.nullcontext()
+    elif not stream:
+        on = torch.cuda.stream(torch.cuda.default_stream())
+    else:
+        on = torch.cuda.stream(torch.cuda.ExternalStream(stream))
+    with on:
         torch.cuda.synchronize()
-        ta = time.perf_counter()
-        if batch is not None:
-            batch.run(prms, scheds, steps, stream)
-        else:
-            for ctx, prm, sched, R in zip(ctxs, prms, scheds, Rs):
-                ctx.run(prm, None, None, steps, sched, stream, n_runs=R)
-        torch.cuda.synchronize()
-        out.integrate_seconds += time.perf_counter() - ta
+        per = []
+        for ctx, prm, sched, h, R, ss in zip(ctxs, prms, scheds, hs, Rs, seed_streams):
+            ctx.run(prm, h, ss.take(R), 0, sched, stream)
+            dt = torch.float64 if prm.prec == chym.PREC_FP64 else torch.float32
+            per.append(dict(
+                next_h=0, offs=torch.zeros(R, dtype=torch.int64, device="cuda"),
+                snap=torch.empty(ctx.N * ctx.D * R, dtype=dt, device="cuda"),
+                F=torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda"),
+                E=torch.empty(R, dtype=torch.float64, device="cuda")))
+        R_all = sum(Rs)
+        up_seeds = torch.empty(R_all, dtype=torch.int64).pin_memory()
+        up_pumps = torch.empty(R_all, dtype=torch.int32).pin_memory()
+        d_seeds = torch.empty(R_all, dtype=torch.int64, device="cuda")
+        d_pumps = torch.empty(R_all, dtype=torch.int32, device="cuda")
+        spans = []
 
-    for ci in range(burn_in + chunks):
-        if ci == burn_in:   # start of the counted window
-            torch.cuda.synchronize()
-            out = Outcome()
-            t0 = time.perf_counter()
-        advance(k_dec // 2)
-        if net is not None:
-            for ctx, st, th in zip(ctxs, per, thetas):
-                if th > -np.inf:   # contexts without a threshold never retire
-                    ctx.copy_state_device(st["snap"].data_ptr(), stream)
-        advance(k_dec - k_dec // 2)
-        for i in range(n):
-            ctx, prm, h, R, st = ctxs[i], prms[i], hs[i], Rs[i], per[i]
-            out.run_steps += R * k_dec
-            k_now = ctx.info()[2]
-            ctx.offsets_device(st["offs"].data_ptr(), stream)
-            local = k_now - st["offs"]
-            done = local >= K
-            restart = done.clone()
-            n_dec = n_ret = n_done = n_hit = 0
-            if bool(done.any()):
+        def advance(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if batch is not None:
+                batch.run(prms, scheds, steps, stream)
+            else:
+                for ctx, prm, sched, R in zip(ctxs, prms, scheds, Rs):
+                    ctx.run(prm, None, None, steps, sched, stream, n_runs=R)
+            e1.record()
+            spans.append((e0, e1))
+
+        out = Outcome()
+        t0 = time.perf_counter()
+        for ci in range(burn_in + chunks):
+            if ci == burn_in:   # start of the counted window
+                torch.cuda.synchronize()
+                out = Outcome()
+                spans.clear()
+                t0 = time.perf_counter()
+            if any(gated):      # snapshot at half the decision step for the slope features
+                advance(k_dec // 2)
+                for ctx, st, g in zip(ctxs, per, gated):
+                    if g:
+                        ctx.copy_state_device(st["snap"].data_ptr(), stream)
+                advance(k_dec - k_dec // 2)
+            else:
+                advance(k_dec)
+            counts, orders = [], []
+            for i in range(n):
+                ctx, R, st = ctxs[i], Rs[i], per[i]
+                out.run_steps += R * k_dec
+                ctx.offsets_device(st["offs"].data_ptr(), stream)
+                local = ctx.info()[2] - st["offs"]
+                done = local >= K
                 ctx.energy_device(st["E"].data_ptr(), 0, stream)
-                hit = (st["E"] - E_gss[i]).abs() <= 1e-9 * max(1.0, abs(E_gss[i]))
-                n_hit = int((hit & done).sum().item())
-                n_done = int(done.sum().item())
+                hit = done & ((st["E"] - E_gss[i]).abs() <= 1e-9 * max(1.0, abs(E_gss[i])))
+                at_dec = local == k_dec
+                retire = torch.zeros_like(done)
+                if gated[i]:
+                    ctx.features_device(st["snap"].data_ptr(), k_dec / K, st["F"].data_ptr(), stream)
+                    retire = at_dec & (logits(net, st["F"], stream) < thetas[i])
+                else:
+                    at_dec = torch.zeros_like(done)
+                restart = done | retire
+                counts.append(torch.stack([at_dec.sum(), retire.sum(), done.sum(), hit.sum(),
+                                           restart.sum()]))
+                # restarted slots first, in increasing slot order
+                orders.append(torch.argsort((~restart).to(torch.int8), stable=True).to(torch.int32))
+            c = torch.stack(counts).cpu().numpy()   # the chunk's one meeting with the host
+            base, todo = 0, []
+            for i in range(n):
+                n_dec, n_ret, n_done, n_hit, m = (int(v) for v in c[i])
                 out.hits += n_hit
                 out.completed += n_done
-            if net is not None and thetas[i] > -np.inf:
-                at_dec = local == k_dec
-                if bool(at_dec.any()):
-                    ctx.features_device(st["snap"].data_ptr(), k_dec / K, st["F"].data_ptr(), stream)
-                    z = logits(net, st["F"], stream)
-                    retire = at_dec & (z < thetas[i])
-                    n_dec = int(at_dec.sum().item())
-                    n_ret = int(retire.sum().item())
-                    out.retired += n_ret
-                    restart |= retire
-            if trace is not None:
-                trace.append((ci, i, n_dec, n_ret, n_done, n_hit))
-            idx = torch.nonzero(restart).flatten().to(torch.int32)
-            if idx.numel():
-                m = idx.numel()
-                n_h = len(h)
-                fresh = torch.from_numpy(seed_streams[i].take(m).view(np.int64)).cuda()
-                pumps = torch.from_numpy(((st["next_h"] + np.arange(m)) % n_h).astype(np.int32)).cuda()
-                st["next_h"] = (st["next_h"] + m) % n_h
-                ctx.reseed_device(idx.data_ptr(), m, fresh.data_ptr(), prm.init_std, pumps.data_ptr(),
-                                  stream)
-                torch.cuda.synchronize()
-    torch.cuda.synchronize()
-    out.seconds = time.perf_counter() - t0
+                out.retired += n_ret
+                if trace is not None:
+                    trace.append((ci, i, n_dec, n_ret, n_done, n_hit))
+                if m:
+                    n_h, st = len(hs[i]), per[i]
+                    up_seeds[base:base + m] = torch.from_numpy(seed_streams[i].take(m).view(np.int64))
+                    up_pumps[base:base + m] = torch.from_numpy(
+                        ((st["next_h"] + np.arange(m)) % n_h).astype(np.int32))
+                    st["next_h"] = (st["next_h"] + m) % n_h
+                    todo.append((i, base, m))
+                    base += m
+            if base:
+                d_seeds[:base].copy_(up_seeds[:base], non_blocking=True)
+                d_pumps[:base].copy_(up_pumps[:base], non_blocking=True)
+                for i, b0, m in todo:
+                    ctxs[i].reseed_device(orders[i].data_ptr(), m, d_seeds[b0:].data_ptr(),
+                                          prms[i].init_std, d_pumps[b0:].data_ptr(), stream)
+        torch.cuda.synchronize()
+        out.seconds = time.perf_counter() - t0
+        out.integrate_seconds = sum(e0.elapsed_time(e1) for e0, e1 in spans) / 1e3
     return out

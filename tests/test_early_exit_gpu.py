@@ -185,3 +185,81 @@ def test_learned_early_exit_gains_over_the_plain_method(torch):
     assert learned.hits_per_mstep > 1.05 * plain.hits_per_mstep
     net.close()
     ctx.close()
+
+
+def _continuous_host_reference(torch, ctx, prm, sched, h, R, ss, K, k_dec, E_gs, chunks, net, theta):
+    """Continuous operation with every decision taken on the host, chunk by chunk:
+    the plain statement of the retire-and-reseed rule that the device-side
+    bookkeeping of early_exit.continuous_many must reproduce exactly."""
+    from paper_2308_02329_gb300 import early_exit as EE
+    trace = []
+    ctx.run(prm, h, ss.take(R), 0, sched)
+    offs = torch.zeros(R, dtype=torch.int64, device="cuda")
+    snap = torch.empty(ctx.N * ctx.D * R, dtype=torch.float32, device="cuda")
+    F = torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda")
+    E = torch.empty(R, dtype=torch.float64, device="cuda")
+    next_h = 0
+    for ci in range(chunks):
+        ctx.run(prm, None, None, k_dec // 2, sched, n_runs=R)
+        ctx.copy_state_device(snap.data_ptr())
+        ctx.run(prm, None, None, k_dec - k_dec // 2, sched, n_runs=R)
+        ctx.offsets_device(offs.data_ptr())
+        local = ctx.info()[2] - offs.cpu().numpy()
+        done = local >= K
+        ctx.energy_device(E.data_ptr())
+        hit = done & (np.abs(E.cpu().numpy() - E_gs) <= 1e-9 * max(1.0, abs(E_gs)))
+        at_dec = np.zeros(R, dtype=bool)
+        retire = np.zeros(R, dtype=bool)
+        if net is not None:
+            at_dec = local == k_dec
+            ctx.features_device(snap.data_ptr(), k_dec / K, F.data_ptr())
+            retire = at_dec & (EE.logits(net, F).cpu().numpy() < theta)
+        restart = done | retire
+        trace.append((ci, 0, int(at_dec.sum()), int(retire.sum()), int(done.sum()), int(hit.sum())))
+        idx = np.flatnonzero(restart).astype(np.int32)
+        if len(idx):
+            m = len(idx)
+            fresh = torch.from_numpy(ss.take(m).view(np.int64)).cuda()
+            pumps = torch.from_numpy(((next_h + np.arange(m)) % len(h)).astype(np.int32)).cuda()
+            next_h = (next_h + m) % len(h)
+            d_idx = torch.from_numpy(idx).cuda()
+            ctx.reseed_device(d_idx.data_ptr(), m, fresh.data_ptr(), prm.init_std, pumps.data_ptr())
+            torch.cuda.synchronize()
+    return trace, ctx.get_state()[0]
+
+
+@pytest.mark.parametrize("with_net", [False, True])
+def test_continuous_bookkeeping_matches_host_reference(torch, with_net):
+    """The device-side retire-and-reseed bookkeeping (one host meeting per chunk) gives
+    the same decisions, retirements, completions, hits and final states as the
+    host-driven statement of the rule, on a case where runs finish, are retired and
+    reseeded many times over."""
+    from paper_2308_02329_gb300 import early_exit as EE
+    N, D, K, k_dec, n_h, R, chunks = 24, 3, 400, 40, 4, 64, 30
+    J = inputs.sk_pm1(N, 78)
+    E_gs = O.ground_state_bruteforce(J)[0]
+    h = inputs.pump_grid(0.5, n_h)
+    net, theta = None, -np.inf
+    a = chym.Context(J, D)
+    prm = chym.Params(eps=0.5 / a.lambda_max(), prec=chym.PREC_BF16X2)
+    sched = chym.Schedule(1, K // 2, K)
+    if with_net:
+        net = chym.MLP(seed=4, max_batch=1024)
+        F, _, _ = EE.generate(a, prm, sched, h, inputs.run_seeds(5, R), K, k_dec, E_gs)
+        theta = float(np.median(EE.logits(net, F).cpu().numpy()))   # retires about half
+    b = chym.Context(J, D)
+    ref_trace, ref_X = _continuous_host_reference(torch, a, prm, sched, h, R, EE.SeedStream(9), K, k_dec,
+                                                  E_gs, chunks, net, theta)
+    trace = []
+    out = EE.continuous_many([b], [prm], [sched], [h], [R], [EE.SeedStream(9)], K, k_dec, [E_gs],
+                             chunks, net, theta, trace=trace)
+    assert trace == ref_trace
+    assert out.completed == sum(t[4] for t in ref_trace) > 0
+    assert out.hits == sum(t[5] for t in ref_trace)
+    if with_net:
+        assert 0 < out.retired == sum(t[3] for t in ref_trace)
+    assert np.array_equal(b.get_state()[0], ref_X)
+    if net is not None:
+        net.close()
+    a.close()
+    b.close()
