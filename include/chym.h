@@ -152,7 +152,8 @@ CHYM_API chym_status chym_energy_device(chym_ctx* ctx, double* d_E, uint64_t* d_
  * lowest energy E = -sum_{p,q} J_pq s_p s_q, over all axes (the pattern changes
  * only where u is perpendicular to a spin; phi and phi + pi give opposite patterns
  * of equal energy).  A spin of zero length reads +1.  Same outputs and layouts as
- * chym_energy; the lowest energy is unique, its pattern is the first reached when
+ * chym_energy (E = NaN for a run whose state is not finite, its spins then
+ * unspecified); the lowest energy is unique, its pattern is the first reached when
  * the axis turns from inside the interval that wraps through pi.  EINVAL unless
  * D = 2 and N <= 4096; ESTATE without a state.  chym_readout_xy writes into the
  * context's energy buffers (the cached Ising energies of chym_energy are dropped)

@@ -14,6 +14,8 @@
 //      moves by 2 J_qp s_p; after the last spin of a group of equal angles the
 //      energy is a candidate; the lowest one (first in sweep order) wins;
 //   5. the winning pattern is rebuilt and bit-packed.
+// A run whose state holds a non-finite value (a diverged run) gets E = NaN, as in
+// the Ising readout, and no sweep; its spins are then unspecified.
 #include <math.h>
 
 #include "chym_internal.cuh"
@@ -37,8 +39,10 @@ __global__ void __launch_bounds__(kXyThreads) round_xy_kernel(const T* __restric
   int8_t* s = reinterpret_cast<int8_t*>(idx + P2);           // N spins
   __shared__ double red[kXyThreads / 32];
   __shared__ double s_phi0;
-  __shared__ int s_live;
+  __shared__ int s_live, s_bad;
   const int run = blockIdx.x, tid = threadIdx.x;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
   const T* x = X + (size_t)run * N * 2;
   const double pi = 3.14159265358979323846;
   // 1. critical angles; spins of zero length never flip (key +inf)
@@ -46,7 +50,8 @@ __global__ void __launch_bounds__(kXyThreads) round_xy_kernel(const T* __restric
     double k = INFINITY;
     if (i < N) {
       const double a = (double)x[2 * (size_t)i], b = (double)x[2 * (size_t)i + 1];
-      if (a != 0.0 || b != 0.0) {
+      if (!isfinite(a) || !isfinite(b)) s_bad = 1;
+      else if (a != 0.0 || b != 0.0) {
         k = fmod(atan2(b, a) + 0.5 * pi, pi);
         if (k < 0.0) k += pi;
       }
@@ -78,6 +83,7 @@ __global__ void __launch_bounds__(kXyThreads) round_xy_kernel(const T* __restric
   if (tid == 0) {
     int live = 0;
     while (live < N && key[live] < INFINITY) ++live;
+    if (s_bad) live = 0;
     s_live = live;
     // an axis inside the interval that wraps from the last critical angle through pi
     s_phi0 = live > 0 ? 0.5 * (key[live - 1] + key[0] + pi) : 0.0;
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(kXyThreads) round_xy_kernel(const T* __restric
   __syncthreads();
   for (int i = tid; i <= best_i; i += blockDim.x) s[idx[i]] = (int8_t)(-s[idx[i]]);
   __syncthreads();
-  if (tid == 0) E_out[run] = best;
+  if (tid == 0) E_out[run] = s_bad ? (double)NAN : best;
   if (spins_out) {
     const int words = (N + 63) / 64;
     for (int wd = tid; wd < words; wd += blockDim.x) {

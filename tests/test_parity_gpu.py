@@ -649,3 +649,35 @@ def test_reseeded_runs_restart_at_local_step_zero(N, D, prec, tol):
     assert _rel_err(X[rest], Xo_rest) <= tol
     assert _rel_err(X[picked], Xo_new) <= tol
     ctx.close()
+
+
+@pytest.mark.parametrize("N,D,prec", [(40, 2, chym.PREC_BF16X2), (40, 2, chym.PREC_FP64),
+                                      (150, 2, chym.PREC_BF16X2)])
+def test_diverged_runs_are_flagged_not_counted(N, D, prec):
+    """Runs whose state holds an infinity or a NaN (a diverged run) read out as NaN energies
+    in both readouts, count neither as hits nor in the energy statistics, and leave the
+    other runs' results untouched."""
+    J, eps, h, seeds = make_case(N, D, 2, 4, 5, "sk")
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=prec)
+    ctx.run(prm, h, seeds, 20, chym.Schedule(0, 0, 20))
+    X, k = ctx.get_state()
+    X[1, 3, 0] = np.inf
+    X[5, 0, 1] = np.nan
+    ctx.set_state(X, h, seeds, k, prec)
+    E = ctx.energy()
+    bad = np.zeros(len(seeds), dtype=bool)
+    bad[[1, 5]] = True
+    assert np.all(np.isnan(E[bad])) and np.all(np.isfinite(E[~bad]))
+    s = np.where(X[:, :, 0] >= 0, 1, -1).astype(np.int8)
+    assert np.array_equal(E[~bad], O.ising_energies(J, s)[~bad])
+    E_gs = float(np.min(E[~bad]))
+    st = ctx.stats(E_gs)
+    assert int(st["n_finite"]) == int(np.sum(~bad))
+    assert int(st["n_hits"]) == int(np.sum(E[~bad] == E_gs))
+    assert st["dE_mean"] == pytest.approx(np.mean(E[~bad] - E_gs), rel=1e-12, abs=1e-12)
+    Exy = ctx.readout_xy()
+    assert np.all(np.isnan(Exy[bad])) and np.all(np.isfinite(Exy[~bad]))
+    for r in np.flatnonzero(~bad):
+        assert Exy[r] == O.round_xy(J, X[r])[0]
+    ctx.close()

@@ -98,12 +98,15 @@ def _map_on_gpu(J, D, gains, replicas, trips, prec, sigma, seed=3):
 @pytest.mark.parametrize("N,D,prec,trips,tol", [
     (20, 3, chym.PREC_FP64, 60, 1e-10),
     (37, 8, chym.PREC_FP64, 40, 1e-10),
+    (45, 2, chym.PREC_FP32, 30, 1e-4),      # SIMT FP32 path
     (100, 4, chym.PREC_BF16X2, 30, 1e-3),   # small-N tensor-core path
+    (61, 1, chym.PREC_BF16X2, 30, 1e-3),    # the CIM as a map (D = 1)
     (150, 2, chym.PREC_BF16X2, 30, 1e-3),   # large-N tensor-core path
 ])
 def test_map_mode_matches_the_literal_map(N, D, prec, trips, tol):
     """Kernels in map mode (three gains around threshold, one batch) against the literal
-    map of Eq. 1 and Eq. 2.  FP64: 1e-10 relative.  BF16 hi+lo: x carries about 16
+    map of Eq. 1 and Eq. 2.  FP64: 1e-10 relative.  FP32: 30 trips of FP32 rounding
+    (2^-24 each, a few operations deep) stay far below 1e-4.  BF16 hi+lo: x carries about 16
     significant bits and dt = 1 leaves the per-trip rounding (~2^-16) undamped, so over
     30 trips the relative error stays below 30 * 2^-16 = 4.6e-4; the test takes 1e-3."""
     torch = pytest.importorskip("torch")
