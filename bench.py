@@ -358,6 +358,39 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def pack_jobs(jobs, lams, graphs, prec, torch):
+    """Fig. 4 graphs of each machine mode packed into contexts of up to 128 spins (blocks
+    of a block-diagonal J; each graph keeps eps_i = eps_hat / lambda_max(J_i) through the
+    per-spin coupling weights, so all share the pump grid).  A pack job reads its
+    graphs' energies as segments."""
+    from paper_2308_02329_gb300 import chym, packing
+    by_mode = {}
+    for j, lam in zip(jobs, lams):
+        by_mode.setdefault(j["mode"], []).append((j, lam))
+    out = []
+    for mode, items in by_mode.items():
+        for k, members in enumerate(packing.plan([j["N"] for j, _ in items])):
+            P = packing.build([graphs[items[i][0]["name"]] for i in members], list(range(len(members))))
+            j0 = items[members[0]][0]
+            ctx = chym.Context(P.J, j0["D"])
+            ctx.set_coupling_weights(packing.spin_weights(
+                P, [1.0 / items[i][1] if items[i][1] > 0 else 0.0 for i in members]))
+            prm = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=j0["gamma"], kappa=j0["kappa"],
+                              eps=EPS_HAT, prec=prec)
+            out.append(dict(j0, name=f"pack{k}_{mode}", N=P.N, ctx=ctx, prm=prm, seg=P.seg_begin,
+                            members=[items[i][0]["name"] for i in members],
+                            nnz=max(1, int((P.J != 0).sum(1).mean()))))
+        for j, _ in items:
+            j["ctx"].close()
+    return out
+
+
+def pack_hits(j, gs, sp):
+    """Ground-state hits of a pack job's graphs, from their segment energies."""
+    Eseg = j["ctx"].energy_segments(j["seg"], sp)
+    return sum(int(np.sum(Eseg[:, b] == gs[m])) for b, m in enumerate(j["members"])), Eseg
+
+
 def learned_leg(jobs, w, sim_steps, gs, batch, stream, chunks, plain):
     """Mixed precision + learned early exit on the same contexts.
 
@@ -465,6 +498,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-pack", action="store_true",
+                    help="fig4: one context per graph instead of graphs packed into 128-spin contexts")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the planner's default cost model instead of measuring it")
     ap.add_argument("--learned-chunks", type=int, default=30,
@@ -549,6 +584,8 @@ def main():
             j["prm"] = chym.Params(dt=dt, sigma=sg, init_std=i0, gamma=ga, kappa=ka, eps=ep, prec=prec)
             j["h"] = np.array([h])
             j["d_h"] = torch.from_numpy(j["h"]).to(dev)
+    if w.key == "fig4" and not args.no_pack:
+        jobs = pack_jobs(jobs, lams, graphs, prec, torch)
     graphs.clear()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     streams = [torch.cuda.Stream(dev) for _ in jobs]
@@ -578,12 +615,14 @@ def main():
         batch.run([j["prm"] for j in jobs], [j["sched"] for j in jobs], sim_steps, sp)
         e1.record(stream)
         for j in jobs:
-            j["ctx"].energy_device(j["d_E"].data_ptr(), 0, sp)
+            if "seg" not in j:
+                j["ctx"].energy_device(j["d_E"].data_ptr(), 0, sp)
         hits = 0
         if record:
             spans.append((e0, [(e0, e1)]))
             for j in jobs:
-                hits += int(j["ctx"].stats(gs[j["name"]], 0, sp)["n_hits"])
+                hits += pack_hits(j, gs, sp)[0] if "seg" in j else \
+                    int(j["ctx"].stats(gs[j["name"]], 0, sp)["n_hits"])
         return hits
 
     def set_prec(pv):
@@ -614,7 +653,12 @@ def main():
         one_step()
     torch.cuda.synchronize()
     for j in jobs:
-        if j["name"] != "moebius":
+        if "seg" in j:
+            Eseg = pack_hits(j, gs, stream.cuda_stream)[1]
+            for b, m in enumerate(j["members"]):
+                if np.isfinite(Eseg[:, b]).any():
+                    gs[m] = min(gs[m], float(np.nanmin(Eseg[:, b])))
+        elif j["name"] != "moebius":
             gs[j["name"]] = min(gs[j["name"]], float(j["d_E"].min().item()))
 
     # ---------------- timed region: device-resident inputs ----------------
@@ -685,6 +729,9 @@ def main():
                 j["ctx"].run(j["prm"], ph.numpy(), ps.numpy().view(np.uint64), 0, j["sched"], sp)
             batch.run([j["prm"] for j in jobs], [j["sched"] for j in jobs], sim_steps, sp)
             for j, eh in zip(jobs, E_host):
+                if "seg" in j:
+                    pack_hits(j, gs, sp)
+                    continue
                 eh.copy_(torch.from_numpy(j["ctx"].energy(stream=sp)))
                 j["ctx"].stats(gs[j["name"]], 0, sp)
         torch.cuda.synchronize()
@@ -692,7 +739,8 @@ def main():
         if world > 1:
             el2, _ = merge_over_ranks(el2, 0, dist, dev)
         h2d = sum(j["n_h"] * 8 + j["runs"] * 8 for j in jobs)
-        d2h = sum(j["runs"] * 8 + 64 + j["n_h"] * 8 for j in jobs)
+        d2h = sum(j["runs"] * 8 * len(j["members"]) if "seg" in j else j["runs"] * 8 + 64 + j["n_h"] * 8
+                  for j in jobs)
         e2e = {"value": work_step * args.steps * world / el2, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
@@ -702,11 +750,16 @@ def main():
         from paper_2308_02329_gb300 import scaling
         rows = {}
         for j in jobs:   # figures of the last timed step's runs
-            st = j["ctx"].stats(gs[j["name"]], 0, stream.cuda_stream)
-            g = int(j["name"].split("_")[1])
-            rows.setdefault(j["mode"], []).append(scaling.GraphResult(
-                j["N"], g, float(gs[j["name"]]), j["N"] <= 24, float(st["P_max"]),
-                float(st["W_range"]), float(st["W_scan"]), float(st["dE_mean"])))
+            if "seg" in j:
+                Eseg = pack_hits(j, gs, stream.cuda_stream)[1]
+                per = [(m, scaling.figures(Eseg[:, b], gs[m], j["n_h"])) for b, m in enumerate(j["members"])]
+            else:
+                per = [(j["name"], j["ctx"].stats(gs[j["name"]], 0, stream.cuda_stream))]
+            for m, st in per:
+                Nm, g = int(m.split("_")[0][len("sparse"):]), int(m.split("_")[1])
+                rows.setdefault(j["mode"], []).append(scaling.GraphResult(
+                    Nm, g, float(gs[m]), Nm <= 24, float(st["P_max"]),
+                    float(st["W_range"]), float(st["W_scan"]), float(st["dE_mean"])))
         scaling_study = {}
         for mode, rs in rows.items():
             agg = scaling.aggregate(rs)
@@ -755,6 +808,12 @@ def main():
             line["tuning"] = tuning
         if scaling_study is not None:
             line["scaling_study"] = scaling_study
+        if w.key == "fig4":
+            line["packing"] = None if args.no_pack else {
+                "contexts": len(jobs), "graphs": sum(len(j["members"]) for j in jobs),
+                "lanes_used": sum(j["N"] for j in jobs) / (128.0 * len(jobs)),
+                "form": "graphs packed into contexts of up to 128 spins (block-diagonal J, "
+                        "eps_i per graph through per-spin coupling weights)"}
         if learned is not None:
             line["learned"] = learned
             line["gs_hits_ratio_learned_vs_plain"] = learned.get("ratio_vs_plain_fp32")

@@ -173,6 +173,26 @@ CHYM_API chym_status chym_readout_xy_device(chym_ctx* ctx, double* d_E, uint64_t
 CHYM_API chym_status chym_stats(chym_ctx* ctx, double E_gs, chym_stats_t* out, int64_t* hits_per_h,
                        int64_t* hist, int n_bins, void* cuda_stream);
 
+/* Per-spin weights of the coupling term: spin p's term eps alpha_mu y_p becomes
+ * eps w_p alpha_mu y_p in every following step (w: N finite doubles, host, copied;
+ * NULL restores w = 1).  This lets independent graphs share one context as the
+ * blocks of a block-diagonal J, each with its own eps_i = eps w_p (the text after
+ * Eq. 1 fixes the coupling per graph, and eps = eps_hat / lambda_max differs
+ * between graphs); the noise counters of a packed graph use its spins' indices in
+ * the packed J.  Weights are supported on the FP64/FP32 paths and on the tensor-core
+ * path up to N = 128 (chym_run and chym_batch_run return ENOTSUP beyond). */
+CHYM_API chym_status chym_set_coupling_weights(chym_ctx* ctx, const double* w);
+
+/* Ising energies of contiguous spin segments [seg_begin[i], seg_begin[i+1]),
+ * i < n_seg (seg_begin: n_seg + 1 ints, host, 0 first and N last, strictly
+ * increasing, 1 <= n_seg <= 128): E_out[run * n_seg + i] = -sum_{p,q in segment i}
+ * J_pq s_p s_q with s_p = sign x_{p,0} (Eq. 3 restricted to one block of a packed
+ * block-diagonal J); exact integers for CHYM_J_PM1, NaN for a segment whose state
+ * is not finite.  E_out: n_runs * n_seg doubles (host).  Does not touch the
+ * energies chym_stats uses.  Synchronises the stream. */
+CHYM_API chym_status chym_energy_segments(chym_ctx* ctx, int n_seg, const int* seg_begin,
+                                          double* E_out, void* cuda_stream);
+
 /* Copy the run state to the host as FP64, layout X[run][p][mu] (n_runs*N*D
  * doubles), and the current step.  Synchronises the stream. */
 CHYM_API chym_status chym_get_state(chym_ctx* ctx, double* X_out, int64_t* k_out, void* cuda_stream);

@@ -23,7 +23,8 @@ _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENO
 
 EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", "chym_run",
            "chym_run_device", "chym_energy", "chym_energy_device", "chym_readout_xy",
-           "chym_readout_xy_device", "chym_stats",
+           "chym_readout_xy_device", "chym_stats", "chym_set_coupling_weights",
+           "chym_energy_segments",
            "chym_get_state", "chym_set_state", "chym_info", "chym_ground_state_exact",
            "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
            "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
@@ -108,6 +109,8 @@ def lib():
         L.chym_energy.argtypes = [vp, vp, vp, vp]
         L.chym_energy_device.argtypes = [vp, vp, vp, vp]
         L.chym_readout_xy.argtypes = [vp, vp, vp, vp]
+        L.chym_set_coupling_weights.argtypes = [vp, vp]
+        L.chym_energy_segments.argtypes = [vp, i32, vp, vp, vp]
         L.chym_readout_xy_device.argtypes = [vp, vp, vp, vp]
         L.chym_stats.argtypes = [vp, dbl, ctypes.POINTER(CStats), vp, vp, i32, vp]
         L.chym_get_state.argtypes = [vp, vp, ctypes.POINTER(i64), vp]
@@ -215,6 +218,24 @@ class Context:
     def energy_device(self, d_E, d_spins=0, stream=0):
         _check(lib().chym_energy_device(self._h, ctypes.c_void_p(d_E), ctypes.c_void_p(d_spins),
                                         ctypes.c_void_p(stream)))
+
+    def set_coupling_weights(self, w=None):
+        """Per-spin weights of the coupling term (chym_set_coupling_weights); None clears."""
+        if w is None:
+            _check(lib().chym_set_coupling_weights(self._h, None))
+            return
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        assert w.shape == (self.N,)
+        _check(lib().chym_set_coupling_weights(self._h, _ptr(w)))
+
+    def energy_segments(self, seg_begin, stream=0):
+        """Ising energies of the spin segments [seg_begin[i], seg_begin[i+1]):
+        array [n_runs, n_seg] (chym_energy_segments)."""
+        b = np.ascontiguousarray(seg_begin, dtype=np.int32)
+        n_seg = len(b) - 1
+        E = np.zeros((self.info()[0], n_seg), dtype=np.float64)
+        _check(lib().chym_energy_segments(self._h, n_seg, _ptr(b), _ptr(E), ctypes.c_void_p(stream)))
+        return E
 
     def readout_xy(self, spins=False, stream=0):
         """Best-axis rounding of D = 2 runs (chym_readout_xy): energies (and packed spins)."""

@@ -115,6 +115,7 @@ StepConsts make_step_consts(const chym_ctx* c, const chym_params* prm, const chy
   sc.k_total = s->k_total;
   sc.koff = c->d_koff;
   sc.hidx = c->d_hidx;
+  sc.w = c->d_w;
   return sc;
 }
 
@@ -137,6 +138,8 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
     c->prec = prm->prec;
   }
   c->have_energy = false;
+  if (steps > 0 && c->d_w && c->N > 128 && c->prec == CHYM_PREC_BF16X2)
+    return fail(CHYM_ENOTSUP, "coupling weights need N <= 128 on the tensor-core path");
   if (steps > 0) {
     const StepConsts sc = make_step_consts(c, prm, sched, c->k, steps);
     cudaError_t e = launch_step(c, sc, c->prec, st);
@@ -262,6 +265,8 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_hidx);
   free_dev(c->d_E);
   free_dev(c->d_spins);
+  free_dev(c->d_w);
+  free_dev(c->d_Eseg);
   free_dev(c->d_status);
   free_dev(c->d_scratch);
   free_dev(c->d_Ak2);
@@ -373,6 +378,46 @@ chym_status chym_energy(chym_ctx* c, double* E_out, uint64_t* spins_out, void* s
     CHYM_CUDA_TRY(cudaMemcpyAsync(spins_out, c->d_spins, sizeof(uint64_t) * c->n_runs * words,
                                   cudaMemcpyDeviceToHost, st));
   }
+  CHYM_CUDA_TRY(cudaStreamSynchronize(st));
+  return check_device_status(c);
+}
+
+chym_status chym_set_coupling_weights(chym_ctx* c, const double* w) {
+  if (!c) return fail(CHYM_EINVAL, "ctx is NULL");
+  if (!w) {
+    free_dev(c->d_w);
+    return CHYM_OK;
+  }
+  for (int p = 0; p < c->N; ++p)
+    if (!isfinite(w[p])) return fail(CHYM_EINVAL, "coupling weights must be finite");
+  if (!c->d_w) CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_w, sizeof(double) * c->N));
+  CHYM_CUDA_TRY(cudaMemcpy(c->d_w, w, sizeof(double) * c->N, cudaMemcpyHostToDevice));
+  return CHYM_OK;
+}
+
+chym_status chym_energy_segments(chym_ctx* c, int n_seg, const int* seg_begin, double* E_out,
+                                 void* stream) {
+  if (!c || !seg_begin || !E_out) return fail(CHYM_EINVAL, "NULL argument");
+  if (c->prec < 0) return fail(CHYM_ESTATE, "no state: call chym_run first");
+  if (n_seg < 1 || n_seg > kMaxSegments) return fail(CHYM_EINVAL, "n_seg must be in [1, 128]");
+  if (seg_begin[0] != 0 || seg_begin[n_seg] != c->N)
+    return fail(CHYM_EINVAL, "segments must start at spin 0 and end at spin N");
+  SegTable t;
+  t.n = n_seg;
+  for (int i = 0; i <= n_seg; ++i) {
+    if (i > 0 && seg_begin[i] <= seg_begin[i - 1]) return fail(CHYM_EINVAL, "segments must be non-empty and ordered");
+    t.begin[i] = seg_begin[i];
+  }
+  const size_t need = (size_t)c->n_runs * n_seg;
+  if (need > c->eseg_cap) {
+    free_dev(c->d_Eseg);
+    c->eseg_cap = 0;
+    CHYM_CUDA_TRY(cudaMalloc((void**)&c->d_Eseg, sizeof(double) * need));
+    c->eseg_cap = need;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CHYM_CUDA_TRY(launch_energy_segments(c, t, c->d_Eseg, st));
+  CHYM_CUDA_TRY(cudaMemcpyAsync(E_out, c->d_Eseg, sizeof(double) * need, cudaMemcpyDeviceToHost, st));
   CHYM_CUDA_TRY(cudaStreamSynchronize(st));
   return check_device_status(c);
 }

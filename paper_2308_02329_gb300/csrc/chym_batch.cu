@@ -163,6 +163,8 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
       return fail(CHYM_EINVAL, "bad params in the batch");
     if ((c->prec == CHYM_PREC_FP64) != (p.prec == CHYM_PREC_FP64))
       return fail(CHYM_EINVAL, "a context cannot change between FP64 and FP32 storage");
+    if (c->d_w && c->N > 128 && p.prec == CHYM_PREC_BF16X2)
+      return fail(CHYM_ENOTSUP, "coupling weights need N <= 128 on the tensor-core path");
     if ((s.kind != 0 && s.kind != 1) || s.reserved != 0 ||
         (s.kind == 1 && (s.k_anneal < 0 || s.k_total <= s.k_anneal)))
       return fail(CHYM_EINVAL, "bad schedule in the batch");

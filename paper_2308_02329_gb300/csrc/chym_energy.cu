@@ -83,6 +83,51 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(
   }
 }
 
+// One CTA per (run, segment): the Ising energy of the segment's spins alone,
+// E_i = -sum_{p,q in i} J_pq s_p s_q (the energy of one graph of a block-diagonal
+// packing); NaN when a state value of the segment is not finite.
+template <typename T, bool PM1>
+__global__ void __launch_bounds__(kEnergyThreads) energy_segments_kernel(
+    const T* __restrict__ X, int N, int D, const int8_t* __restrict__ J8,
+    const double* __restrict__ J64, SegTable t, double* __restrict__ E) {
+  extern __shared__ int8_t s[];
+  __shared__ int bad;
+  __shared__ long long red_i[32];
+  __shared__ double red_d[32];
+  const int run = blockIdx.x, seg = blockIdx.y, tid = threadIdx.x;
+  const int b = t.begin[seg], n = t.begin[seg + 1] - b;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  const T* x = X + ((size_t)run * N + b) * D;
+  int my_bad = 0;
+  for (int p = tid; p < n; p += blockDim.x) {
+    s[p] = (x[(size_t)p * D] >= T(0)) ? 1 : -1;
+    for (int mu = 0; mu < D; ++mu) my_bad |= !isfinite((double)x[(size_t)p * D + mu]);
+  }
+  if (my_bad) atomicOr(&bad, 1);
+  __syncthreads();
+  double* out = E + (size_t)run * t.n + seg;
+  if (PM1) {
+    long long acc = 0;
+    for (int p = tid; p < n; p += blockDim.x) {
+      int f = 0;
+      for (int q = 0; q < n; ++q) f += (int)J8[(size_t)(b + q) * N + b + p] * (int)s[q];
+      acc += (long long)s[p] * f;
+    }
+    const long long tot = block_sum<long long>(acc, red_i);
+    if (tid == 0) *out = bad ? (double)NAN : -(double)tot;
+  } else {
+    double acc = 0.0;
+    for (int p = tid; p < n; p += blockDim.x) {
+      double f = 0.0;
+      for (int q = 0; q < n; ++q) f += J64[(size_t)(b + q) * N + b + p] * (double)s[q];
+      acc += (double)s[p] * f;
+    }
+    const double tot = block_sum<double>(acc, red_d);
+    if (tid == 0) *out = bad ? (double)NAN : -tot;
+  }
+}
+
 // Single CTA, deterministic: per-h hits, histogram, best run, finite count,
 // sum of (E - E_gs) over finite runs.  out layout (see StatsOut).
 struct StatsOut {
@@ -182,6 +227,25 @@ cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStrea
   if (c->n_runs <= 0) return cudaSuccess;
   if (c->prec == CHYM_PREC_FP64) return launch_energy_typed<double>(c, d_E, d_spins, st);
   return launch_energy_typed<float>(c, d_E, d_spins, st);
+}
+
+cudaError_t launch_energy_segments(chym_ctx* c, const SegTable& t, double* d_E, cudaStream_t st) {
+  if (c->n_runs <= 0) return cudaSuccess;
+  int longest = 0;
+  for (int i = 0; i < t.n; ++i) longest = std::max(longest, t.begin[i + 1] - t.begin[i]);
+  const dim3 grid((unsigned)c->n_runs, (unsigned)t.n);
+  const size_t smem = (size_t)longest;
+  const bool pm1 = c->kind == CHYM_J_PM1;
+  if (c->prec == CHYM_PREC_FP64) {
+    const double* X = (const double*)c->d_X;
+    if (pm1) energy_segments_kernel<double, true><<<grid, kEnergyThreads, smem, st>>>(X, c->N, c->D, c->d_J8, c->d_J64, t, d_E);
+    else energy_segments_kernel<double, false><<<grid, kEnergyThreads, smem, st>>>(X, c->N, c->D, c->d_J8, c->d_J64, t, d_E);
+  } else {
+    const float* X = (const float*)c->d_X;
+    if (pm1) energy_segments_kernel<float, true><<<grid, kEnergyThreads, smem, st>>>(X, c->N, c->D, c->d_J8, c->d_J64, t, d_E);
+    else energy_segments_kernel<float, false><<<grid, kEnergyThreads, smem, st>>>(X, c->N, c->D, c->d_J8, c->d_J64, t, d_E);
+  }
+  return cudaGetLastError();
 }
 
 size_t stats_out_bytes(int n_h, int n_bins) {

@@ -40,6 +40,15 @@ struct StepConsts {
   int64_t k_anneal, k_total;
   const int64_t* koff;        // per run: global step at which the run was (re)seeded
   const int32_t* hidx;        // per run: index of its pump value in h
+  const double* w;            // per spin: weight of its coupling term (nullable: all 1)
+};
+
+// Contiguous spin ranges [begin[i], begin[i + 1]) whose Ising energies are read
+// out separately (independent graphs packed into one block-diagonal J).
+constexpr int kMaxSegments = 128;
+struct SegTable {
+  int n;
+  int begin[kMaxSegments + 1];
 };
 
 // Device status word: bit flags raised by kernels, read back by the host.
@@ -160,6 +169,9 @@ struct chym_ctx {
   double* d_E = nullptr;      // energies of the last chym_energy*
   uint64_t* d_spins = nullptr;
   bool have_energy = false;
+  double* d_w = nullptr;      // per spin coupling weights (nullable: all 1)
+  double* d_Eseg = nullptr;   // energies of the last chym_energy_segments, [run][segment]
+  size_t eseg_cap = 0;        // doubles
   unsigned* d_status = nullptr;
   void* d_scratch = nullptr;  // stats scratch
   size_t scratch_bytes = 0;
@@ -205,6 +217,7 @@ cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, con
                             int n_cta, int64_t steps, int kp_max, int terms_max, unsigned* status,
                             cudaStream_t st);
 cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st);
+cudaError_t launch_energy_segments(chym_ctx* c, const SegTable& t, double* d_E, cudaStream_t st);
 cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol, double bin_w,
                          int n_bins, void* d_out, cudaStream_t st);
 double host_lambda_max(const double* J, int N);

@@ -144,9 +144,10 @@ __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg
       T ramp = T(1);  // alpha_mu(kl) for mu >= 1; mu = 0 keeps alpha = 1
       if (sc.sched_kind == 1 && kl >= sc.k_anneal)
         ramp = kl >= sc.k_total ? T(0) : T(1) - (T)(kl - sc.k_anneal) * inv_ramp;
+      const T wp = sc.w ? (T)sc.w[p] : T(1);  // this spin's coupling weight
       T ea[D];
 #pragma unroll
-      for (int mu = 0; mu < D; ++mu) ea[mu] = (T)sc.eps * (mu == 0 ? T(1) : ramp);
+      for (int mu = 0; mu < D; ++mu) ea[mu] = (T)sc.eps * wp * (mu == 0 ? T(1) : ramp);
       const T hm1 = (T)(hg[sc.hidx[run]] - 1.0);
       T* x = Xs + (size_t)s * D;
       const T* y = Ys + (size_t)s * D;

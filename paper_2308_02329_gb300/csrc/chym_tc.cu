@@ -37,6 +37,7 @@ struct TcDesc {
   const uint64_t* seeds;
   const int64_t* koff;  // per run: global step of its (re)seeding
   const int32_t* hidx;  // per run: index of its pump value
+  const double* w;      // per spin: coupling weight (nullable: all 1)
   int N, KP, n_runs, replicas, a_terms, sched_kind;
   int64_t k0, k_anneal, k_total;
   float dt, noise_scale, gdt, kdt, edt, inv_ramp;
@@ -387,6 +388,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
     __syncthreads();  // every zero must land before any thread writes its state into B
     if (p < nr && s_koff[g][p] != s_koff[g][0]) s_kuni[g] = 0;
     const bool live = p < N;
+    const float edt_p = d.edt * ((d.w && live) ? (float)d.w[p] : 1.f);  // dt eps times the spin's weight
     // ---- load the state: X[run][p][mu] -> TMEM master + BF16 hi/lo B ----
     for (int r0 = 0; r0 < nr; r0 += CH) {
 #pragma unroll
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
                   if (klB >= d.k_anneal)
                     rB = klB >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(klB - d.k_anneal) * d.inv_ramp);
                 }
-                const float2 e0 = make_float2(d.edt, d.edt), e1 = make_float2(d.edt * rA, d.edt * rB);
+                const float2 e0 = make_float2(edt_p, edt_p), e1 = make_float2(edt_p * rA, edt_p * rB);
                 float2 z[4 * ((D + 3) / 4)];
                 if constexpr (D == 2) {
                   // spins p and p ^ 1 share one Philox block per run (pair 0: the even
@@ -664,6 +666,7 @@ void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out) {
   d.seeds = c->d_seeds;
   d.koff = c->d_koff;
   d.hidx = c->d_hidx;
+  d.w = sc.w;
   d.N = c->N;
   d.KP = (c->N + 15) / 16 * 16;
   d.n_runs = sc.n_runs;

@@ -3,9 +3,11 @@ around it): the coherent Ising machine (D = 1) against the hyperspin machine wit
 dimensional annealing (D = 2 annealed back to 1), on random sparse +-1 graphs of
 growing N.
 
-Per graph, the figures of merit of the text after Fig. 3 come from the library
-(chym_stats): the best success probability over the pump scan P_max, the
-pump-range weight W and the mean energy gap dE.  Per size N they are averaged over
+Per graph, the figures of merit of the text after Fig. 3 come from its run
+energies: the best success probability over the pump scan P_max, the pump-range
+weight W and the mean energy gap dE.  Graphs of up to 128 spins in total share a
+context as blocks of a block-diagonal J (`packing`), so the small graphs of the scan
+fill the 128 lanes of the tensor-core tile instead of one graph per tile.  Per size N they are averaged over
 the graphs (with the quartiles that Fig. 4 shades), and the decay of the mean
 success probability is fitted as P_max(N) ~ exp(c - a N), the exponent a
 measuring how hard the machine finds larger problems.
@@ -18,7 +20,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import chym, inputs
+from . import chym, inputs, packing
 
 # Machine modes (readings of the text before Fig. 3 and Fig. 4): the CIM has no
 # hyperspin loss (gamma = 0) and only the local saturation kappa; CHYM+DA keeps
@@ -63,39 +65,86 @@ def params_for(mode, lam, steps, eps_hat=0.5, prec=chym.PREC_BF16X2):
     return prm, sched
 
 
-def run(Ns, mode, n_graphs, n_h, reps, steps, density=0.2, seed=0x5CA1E, eps_hat=0.5,
-        exact_max_n=24, stream=0):
-    """Integrate every graph of every size in one batch and return the per-graph
-    figures of merit (list of GraphResult)."""
+def figures(E, E_gs, n_h):
+    """The figures of merit (text after Fig. 3) of one graph from its run energies
+    (h-major runs, as chym_stats counts them): ground-state hits per pump (E == E_GS,
+    exact for the integer energies of +-1 couplings; a diverged run's NaN never
+    counts), P_max, W normalised by the pumps with P > 0 (W_range) and by all scanned
+    pumps (W_scan), and the mean E - E_GS over finite runs."""
+    E = np.asarray(E, dtype=np.float64).reshape(n_h, -1)
+    hits = np.sum(E == E_gs, axis=1).astype(np.int64)
+    P = hits / E.shape[1]
+    nz = int(np.count_nonzero(hits))
+    fin = np.isfinite(E)
+    return {"hits": hits, "P_max": float(P.max()) if n_h else 0.0,
+            "W_range": float(P.sum() / nz) if nz else 0.0, "W_scan": float(P.sum() / n_h),
+            "dE_mean": float(np.mean(E[fin] - E_gs)) if fin.any() else math.nan,
+            "n_hits": int(hits.sum())}
+
+
+def graphs_and_references(Ns, n_graphs, density=0.2, seed=0x5CA1E, exact_max_n=24):
+    """Every graph of the set with lambda_max(J) and its ground-state reference:
+    list of (N, index, seed, J, lambda_max, E_GS, exact)."""
+    out = []
+    for N, g, gseed in graph_set(Ns, n_graphs, density, seed):
+        J = inputs.sparse_pm1(N, density, gseed)
+        c = chym.Context(J, 1)
+        lam = c.lambda_max()
+        E_gs, exact = ground_state(c, exact_max_n)
+        c.close()
+        out.append((N, g, gseed, J, lam, E_gs, exact))
+    return out
+
+
+def pack_contexts(graphs, mode, n_h, reps, steps, eps_hat=0.5, prec=chym.PREC_BF16X2, stream=0,
+                  pack=True):
+    """Contexts of one machine mode over the graph list, several graphs per context as
+    blocks of a block-diagonal J when `pack` (each with its own eps_i through the
+    per-spin coupling weights 1 / lambda_max(J_i)), initialised at step 0.  Returns
+    a list of (context, params, schedule, packing.Pack, seeds, weights); the params'
+    eps is eps_hat."""
     m = MODES[mode]
     D = m["D"]
     h = inputs.pump_grid(1.0 - eps_hat, n_h)
-    ctxs, prms, scheds, meta = [], [], [], []
-    for N, g, gseed in graph_set(Ns, n_graphs, density, seed):
-        J = inputs.sparse_pm1(N, density, gseed)
-        ctx = chym.Context(J, D)
-        lam = ctx.lambda_max()
-        prm, sched = params_for(mode, lam, steps, eps_hat)
-        ctx.run(prm, h, inputs.run_seeds(gseed, n_h * reps), 0, sched, stream)
-        E_gs, exact = ground_state(ctx, exact_max_n)
-        ctxs.append(ctx)
-        prms.append(prm)
-        scheds.append(sched)
-        meta.append((N, g, E_gs, exact))
-    batch = chym.Batch(ctxs)
-    batch.run(prms, scheds, steps, stream)
-    batch.status()
+    groups = packing.plan([gr[0] for gr in graphs]) if pack else [[i] for i in range(len(graphs))]
     out = []
-    for ctx, (N, g, E_gs, exact) in zip(ctxs, meta):
-        E = ctx.energy(stream=stream)
-        if not exact:   # best known: the search's bound or the best run, whichever is lower
-            E_gs = min(E_gs, float(np.min(E)))
-        st = ctx.stats(E_gs, 0, stream)
-        out.append(GraphResult(N, g, float(E_gs), exact, float(st["P_max"]), float(st["W_range"]),
-                               float(st["W_scan"]), float(st["dE_mean"]),
-                               [int(v) for v in st["hits"]]))
-    batch.close()
-    for ctx in ctxs:
+    for members in groups:
+        P = packing.build([gr[3] for gr in graphs], members)
+        ctx = chym.Context(P.J, D)
+        lam = [graphs[i][4] for i in members]
+        w = packing.spin_weights(P, [1.0 / l if l > 0 else 0.0 for l in lam])
+        ctx.set_coupling_weights(w)
+        prm, sched = params_for(mode, 1.0, steps, eps_hat, prec)
+        seeds = inputs.run_seeds(graphs[members[0]][2], n_h * reps)
+        ctx.run(prm, h, seeds, 0, sched, stream)
+        out.append((ctx, prm, sched, P, seeds, w))
+    return out
+
+
+def run(Ns, mode, n_graphs, n_h, reps, steps, density=0.2, seed=0x5CA1E, eps_hat=0.5,
+        exact_max_n=24, stream=0, prec=chym.PREC_BF16X2, pack=True, graphs=None):
+    """Integrate every graph of every size of one machine mode in one batch (small
+    graphs packed several to a context) and return the per-graph figures of merit
+    (list of GraphResult, in graph-set order)."""
+    graphs = graphs or graphs_and_references(Ns, n_graphs, density, seed, exact_max_n)
+    jobs = pack_contexts(graphs, mode, n_h, reps, steps, eps_hat, prec, stream, pack)
+    batch = chym.Batch([j[0] for j in jobs])
+    try:
+        batch.run([j[1] for j in jobs], [j[2] for j in jobs], steps, stream)
+        batch.status()
+    finally:
+        batch.close()
+    out = [None] * len(graphs)
+    for ctx, _, _, P, _, _ in jobs:
+        Eseg = ctx.energy_segments(P.seg_begin, stream)
+        for b, i in enumerate(P.members):
+            N, g, _, _, _, E_gs, exact = graphs[i]
+            E = Eseg[:, b]
+            if not exact:   # best known: the search's bound or the best run, whichever is lower
+                E_gs = min(E_gs, float(np.nanmin(E)) if np.isfinite(E).any() else E_gs)
+            f = figures(E, E_gs, n_h)
+            out[i] = GraphResult(N, g, float(E_gs), exact, f["P_max"], f["W_range"], f["W_scan"],
+                                 f["dE_mean"], [int(v) for v in f["hits"]])
         ctx.close()
     return out
 
@@ -139,9 +188,10 @@ def study(Ns, n_graphs, steps, modes=("cim", "chym_da"), n_h=None, reps=32, dens
     rate of the mean success probability.  n_h defaults to the paper's scans (51
     pump values for the CIM, 21 for CHYM+DA)."""
     res = {}
+    graphs = graphs_and_references(Ns, n_graphs, density, seed)
     for mode in modes:
         nh = n_h or (51 if MODES[mode]["D"] == 1 else 21)
-        rows = run(Ns, mode, n_graphs, nh, reps, steps, density, seed, stream=stream)
+        rows = run(Ns, mode, n_graphs, nh, reps, steps, density, seed, stream=stream, graphs=graphs)
         agg = aggregate(rows)
         a, c, used = fit_exponential(list(agg), [agg[N]["P_max"]["mean"] for N in agg])
         res[mode] = {"n_h": nh, "replicas": reps, "per_N": agg, "decay_a": a, "decay_c": c,

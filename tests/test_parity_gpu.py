@@ -681,3 +681,56 @@ def test_diverged_runs_are_flagged_not_counted(N, D, prec):
     for r in np.flatnonzero(~bad):
         assert Exy[r] == O.round_xy(J, X[r])[0]
     ctx.close()
+
+
+@pytest.mark.parametrize("D,prec,tol", [(2, chym.PREC_FP64, 1e-10), (1, chym.PREC_FP32, 1e-4),
+                                        (2, chym.PREC_BF16X2, 1e-4), (3, chym.PREC_BF16X2, 1e-4)])
+def test_packed_graphs_match_checker(D, prec, tol):
+    """Three sparse graphs packed into one context (block-diagonal J, per-spin coupling
+    weights 1/lambda_max of each graph): the state equals the checker's integration of
+    J' = diag(w) J, and the segment energies equal each graph's own Ising energy of the
+    same state (exact integers)."""
+    from paper_2308_02329_gb300 import packing
+    Js = [inputs.sparse_pm1(n, 0.2, 900 + n) for n in (23, 10, 17)]
+    P = packing.build(Js, [0, 2, 1])
+    lam = [float(np.linalg.eigvalsh(J)[-1]) for J in Js]
+    w = packing.spin_weights(P, [1.0 / lam[i] for i in P.members])
+    n_h, reps, steps = 3, 5, 60
+    h = inputs.pump_grid(0.5, n_h)
+    seeds = inputs.run_seeds(41, n_h * reps)
+    ctx = chym.Context(P.J, D)
+    ctx.set_coupling_weights(w)
+    prm = chym.Params(eps=0.5, prec=prec, kappa=0.1)
+    sch = chym.Schedule(1, steps // 2, steps)
+    ctx.run(prm, h, seeds, steps, sch)
+    X, _ = ctx.get_state()
+    Xo = O.run(w[:, None] * P.J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm),
+               oracle_schedule(sch), steps)
+    assert _rel_err(X, Xo) <= tol
+    Eseg = ctx.energy_segments(P.seg_begin)
+    assert Eseg.shape == (n_h * reps, 3)
+    for b, i in enumerate(P.members):
+        lo, hi = P.seg_begin[b], P.seg_begin[b + 1]
+        assert np.array_equal(Eseg[:, b], O.ising_energies(Js[i], O.readout(X[:, lo:hi, :])))
+    assert np.array_equal(Eseg.sum(axis=1), ctx.energy())   # no coupling between the blocks
+    # clearing the weights restores the plain equations
+    ctx.set_coupling_weights(None)
+    ctx.run(prm, h, seeds, steps, sch)
+    Xp = O.run(P.J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm), oracle_schedule(sch), steps)
+    assert _rel_err(ctx.get_state()[0], Xp) <= tol
+    ctx.close()
+
+
+def test_coupling_weights_arguments():
+    ctx = chym.Context(inputs.sk_pm1(200, 3), 2)
+    with pytest.raises(chym.ChymError):
+        ctx.set_coupling_weights(np.full(200, np.nan))
+    ctx.set_coupling_weights(np.ones(200))
+    prm = chym.Params(eps=0.01, prec=chym.PREC_BF16X2)
+    with pytest.raises(chym.ChymError, match="ENOTSUP"):
+        ctx.run(prm, inputs.pump_grid(0.5, 2), inputs.run_seeds(1, 4), 10, chym.Schedule(0, 0, 10))
+    ctx.run(prm, inputs.pump_grid(0.5, 2), inputs.run_seeds(1, 4), 0, chym.Schedule(0, 0, 10))
+    for bad in ([0, 100], [0, 100, 100, 200], [1, 200], [0, 201]):
+        with pytest.raises(chym.ChymError):
+            ctx.energy_segments(bad)
+    ctx.close()
