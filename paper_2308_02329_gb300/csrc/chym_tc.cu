@@ -290,6 +290,26 @@ __device__ __forceinline__ void box_muller_x2(uint32_t wrA, uint32_t waA, uint32
   zs = __fmul2_rn(r, make_float2(sA, sB));
 }
 
+// The four lanes of a quad hold the rows of a 4 x 4 matrix (lane m: a[m][0..3]);
+// afterwards lane m holds column m (b[i] = a[i][m]).  Two exchange stages: with
+// lane m ^ 1 the columns of the other parity, then with lane m ^ 2 the other half
+// of the lane's own column.
+__device__ __forceinline__ void quad_transpose(float v0, float v1, float v2, float v3, int m, float (&b)[4]) {
+  const bool odd = (m & 1) != 0, high = (m & 2) != 0;
+  const float s0 = odd ? v0 : v1, s1 = odd ? v2 : v3;  // columns of the other parity
+  const float k0 = odd ? v1 : v0, k1 = odd ? v3 : v2;  // columns c0 = m & 1, c1 = c0 + 2
+  const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+  // rows 2h and 2h + 1 (h = m / 2) of columns c0 and c1
+  const float a00 = odd ? r0 : k0, a10 = odd ? k0 : r0, a01 = odd ? r1 : k1, a11 = odd ? k1 : r1;
+  const float se = high ? a00 : a01, so = high ? a10 : a11;  // the column lane m ^ 2 needs
+  const float ke = high ? a01 : a00, ko = high ? a11 : a10;  // column m
+  const float re = __shfl_xor_sync(0xffffffffu, se, 2), ro = __shfl_xor_sync(0xffffffffu, so, 2);
+  b[0] = high ? re : ke;
+  b[1] = high ? ro : ko;
+  b[2] = high ? ke : re;
+  b[3] = high ? ko : ro;
+}
+
 template <int D>
 __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
   using Cfg = TcCfg<D>;
@@ -474,8 +494,9 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
             for (int mu = 0; mu < D; ++mu)
               tmem_ld2_wait<CH>(t_lane + acc_col + (uint32_t)(mu * RG + r0),
                                 t_lane + mst_col + (uint32_t)(mu * RG + r0), y[mu], x[mu]);
-            // D = 2: every lane takes part in the noise (lanes exchange normals)
-            if (live || D == 2) {
+            // D <= 2: every lane takes part in the noise (lanes exchange normals)
+            if (live || D <= 2) {
+              float nq[4];  // D = 1: this spin's normals of four consecutive runs
 #pragma unroll
               for (int j = 0; j < CH; j += 2) {  // two runs at once, FP32x2 arithmetic
                 const int r = r0 + j;
@@ -512,14 +533,19 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
                   z[1] = odd ? make_float2(rs, ks) : make_float2(ks, rs);
                   if (!live) continue;
                 } else if constexpr (D == 1) {
-                  // four spins share one block: spin p takes normal p % 4 of it
-                  const uint32_t j0 = (uint32_t)p & 3u;
-                  const uint4 wA = philox_rk(noise_counter((uint32_t)p >> 2, 0u, 0u, (uint64_t)klA), s_rk[g][r]);
-                  const uint4 wB = philox_rk(noise_counter((uint32_t)p >> 2, 0u, 0u, (uint64_t)klB), s_rk[g][r + 1]);
-                  float2 zc, zs;
-                  if (j0 >= 2u) box_muller_x2(wA.z, wA.w, wB.z, wB.w, neg2ln2s2, zc, zs);
-                  else box_muller_x2(wA.x, wA.y, wB.x, wB.y, neg2ln2s2, zc, zs);
-                  z[0] = (j0 & 1u) ? zs : zc;
+                  // four spins share one block (spin p takes normal p % 4 of it): at every
+                  // fourth run each lane of a quad draws the block of one of the four runs
+                  // and the quad transposes the normals
+                  if ((j & 3) == 0) {
+                    const int m = p & 3, rm = r + m;
+                    const int64_t klm = k_uniform ? kl_u : k - s_koff[g][rm];
+                    const uint4 w = philox_rk(noise_counter((uint32_t)p >> 2, 0u, 0u, (uint64_t)klm), s_rk[g][rm]);
+                    float2 zc, zs;  // normals (0, 2) and (1, 3) of the block
+                    box_muller_x2(w.x, w.y, w.z, w.w, neg2ln2s2, zc, zs);
+                    quad_transpose(zc.x, zs.x, zc.y, zs.y, m, nq);
+                  }
+                  z[0] = (j & 3) == 0 ? make_float2(nq[0], nq[1]) : make_float2(nq[2], nq[3]);
+                  if (!live) continue;
                 } else {
 #pragma unroll
                   for (int blk = 0; blk < (D + 3) / 4; ++blk) {

@@ -621,6 +621,8 @@ def test_uneven_batch_full_size_sampled():
 @pytest.mark.parametrize("N,D,prec,tol", [(24, 3, chym.PREC_FP64, 1e-10),
                                           (100, 4, chym.PREC_BF16X2, 1e-4),
                                           (150, 2, chym.PREC_BF16X2, 1e-4),
+                                          (61, 1, chym.PREC_BF16X2, 1e-4),
+                                          (64, 2, chym.PREC_BF16X2, 1e-4),
                                           (40, 8, chym.PREC_FP32, 1e-4)])
 def test_reseeded_runs_restart_at_local_step_zero(N, D, prec, tol):
     torch = pytest.importorskip("torch")
