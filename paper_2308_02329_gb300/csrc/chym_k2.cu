@@ -757,8 +757,18 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
   std::vector<uint32_t> dim_stride(9, 0);
   for (int D = 1; D <= 8; ++D) {
     dim_first[D] = (int)tiles.size();
-    for (int i = 0; i < n_desc; ++i) {
-      if (dims[i] != D) continue;
+    // contexts in decreasing order of tile cost (K x columns x product terms): the
+    // persistent CTAs take tiles round-robin, so the costly tiles go out first and
+    // the cheap ones fill in at the end (mixed sizes otherwise leave long tails)
+    std::vector<int> order;
+    for (int i = 0; i < n_desc; ++i)
+      if (dims[i] == D) order.push_back(i);
+    auto cost = [&](int i) {
+      const K2Desc& d = *reinterpret_cast<const K2Desc*>(descs.data() + i * db);
+      return (long long)d.KP * d.n * d.a_terms;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    for (int i : order) {
       const K2Desc& d = *reinterpret_cast<const K2Desc*>(descs.data() + i * db);
       const uint32_t bytes = (uint32_t)d.a_terms * kABlock + 2u * b_block_bytes(d.n);
       dim_stride[D] = std::max(dim_stride[D], (bytes + 1023u) / 1024u * 1024u);
