@@ -776,6 +776,12 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
         for (int mt = 0; mt < d.MT; ++mt) tiles.push_back(K2Tile{i, mt, ct, 0});  // mt fastest
     }
     dim_count[D] = (int)tiles.size() - dim_first[D];
+    // boustrophedon rounds: every other full round of `grid` tiles goes to the CTAs in
+    // reverse, so the CTA that drew the largest tile of one round draws the smallest of
+    // the next
+    const int grid = std::min(dim_count[D], max_ctas > 0 ? std::min(max_ctas, R.sms) : R.sms);
+    for (int r0 = grid; grid > 0 && r0 + grid <= dim_count[D]; r0 += 2 * grid)
+      std::reverse(tiles.begin() + dim_first[D] + r0, tiles.begin() + dim_first[D] + r0 + grid);
   }
   const size_t bytes = 64 + descs.size() + tiles.size() * sizeof(K2Tile);
   if (bytes > R.bytes) {
@@ -809,7 +815,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
           (int)std::min<size_t>(kMaxStages, std::max<size_t>(2, kRingBudget / dim_stride[D]));
       // at least 120 KB: one CTA (which owns 512 TMEM columns) per SM
       const size_t smem = std::max<size_t>((size_t)stages * dim_stride[D], 120 * 1024);
-      const int grid = std::min(dim_count[D], max_ctas > 0 ? std::min(max_ctas, R.sms) : R.sms);
+      const int grid = std::min(dim_count[D], max_ctas > 0 ? std::min(max_ctas, R.sms) : R.sms);  // as above
       K2Launch L{d_descs, d_tiles + dim_first[D], d_done, dim_count[D], k_off, stages, dim_stride[D],
                  status};
       cudaError_t r = k2_launch(D, L, grid, smem, s);
