@@ -201,6 +201,7 @@ extern "C" {
 const char* chym_last_error(void) { return g_last_error.c_str(); }
 
 chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx** out) {
+  chym::TraceRange trace_("chym_create");
   if (!out) return fail(CHYM_EINVAL, "out is NULL");
   if (!J) return fail(CHYM_EINVAL, "J is NULL");
   if (N < 1 || N > 4096) return fail(CHYM_EINVAL, "N must be in [1, 4096]");
@@ -286,6 +287,7 @@ chym_status chym_lambda_max(chym_ctx* c, double* out) {
 
 chym_status chym_reseed_device(chym_ctx* c, const int32_t* d_runs, int n, const uint64_t* d_new_seeds,
                                const int32_t* d_new_pump, double init_std, void* stream) {
+  chym::TraceRange trace_("chym_reseed_device");
   if (!c) return fail(CHYM_EINVAL, "ctx is NULL");
   if (c->prec < 0) return fail(CHYM_ESTATE, "no state: call chym_run first");
   if (n < 0 || (n > 0 && (!d_runs || !d_new_seeds))) return fail(CHYM_EINVAL, "bad run list");
@@ -315,6 +317,7 @@ chym_status chym_info(chym_ctx* c, int* n_runs, int* n_h, int64_t* k) {
 chym_status chym_run(chym_ctx* c, const chym_params* prm, const double* h, int n_h,
                      const uint64_t* seeds, int n_runs, int64_t steps,
                      const chym_schedule* sched, void* stream) {
+  chym::TraceRange trace_("chym_run");
   chym_status s = check_run_args(c, prm, n_h, n_runs, steps, sched, seeds != nullptr);
   if (s != CHYM_OK) return s;
   if (!h && seeds) return fail(CHYM_EINVAL, "h is NULL");
@@ -336,6 +339,7 @@ chym_status chym_run(chym_ctx* c, const chym_params* prm, const double* h, int n
 chym_status chym_run_device(chym_ctx* c, const chym_params* prm, const double* d_h, int n_h,
                             const uint64_t* d_seeds, int n_runs, int64_t steps,
                             const chym_schedule* sched, void* stream) {
+  chym::TraceRange trace_("chym_run_device");
   chym_status s = check_run_args(c, prm, n_h, n_runs, steps, sched, d_seeds != nullptr);
   if (s != CHYM_OK) return s;
   if (!d_h && d_seeds) return fail(CHYM_EINVAL, "d_h is NULL");
@@ -356,6 +360,7 @@ chym_status chym_run_device(chym_ctx* c, const chym_params* prm, const double* d
 }
 
 chym_status chym_energy_device(chym_ctx* c, double* d_E, uint64_t* d_spins, void* stream) {
+  chym::TraceRange trace_("chym_energy_device");
   if (!c || !d_E) return fail(CHYM_EINVAL, "NULL argument");
   if (c->prec < 0) return fail(CHYM_ESTATE, "no state: call chym_run first");
   cudaStream_t st = (cudaStream_t)stream;
@@ -367,6 +372,7 @@ chym_status chym_energy_device(chym_ctx* c, double* d_E, uint64_t* d_spins, void
 }
 
 chym_status chym_energy(chym_ctx* c, double* E_out, uint64_t* spins_out, void* stream) {
+  chym::TraceRange trace_("chym_energy");
   if (!c || !E_out) return fail(CHYM_EINVAL, "NULL argument");
   if (c->prec < 0) return fail(CHYM_ESTATE, "no state: call chym_run first");
   cudaStream_t st = (cudaStream_t)stream;
@@ -397,6 +403,7 @@ chym_status chym_set_coupling_weights(chym_ctx* c, const double* w) {
 
 chym_status chym_energy_segments(chym_ctx* c, int n_seg, const int* seg_begin, double* E_out,
                                  void* stream) {
+  chym::TraceRange trace_("chym_energy_segments");
   if (!c || !seg_begin || !E_out) return fail(CHYM_EINVAL, "NULL argument");
   if (c->prec < 0) return fail(CHYM_ESTATE, "no state: call chym_run first");
   if (n_seg < 1 || n_seg > kMaxSegments) return fail(CHYM_EINVAL, "n_seg must be in [1, 128]");
@@ -424,6 +431,7 @@ chym_status chym_energy_segments(chym_ctx* c, int n_seg, const int* seg_begin, d
 
 chym_status chym_stats(chym_ctx* c, double E_gs, chym_stats_t* out, int64_t* hits_per_h,
                        int64_t* hist, int n_bins, void* stream) {
+  chym::TraceRange trace_("chym_stats");
   if (!c || !out) return fail(CHYM_EINVAL, "NULL argument");
   if (!c->have_energy) return fail(CHYM_ESTATE, "call chym_energy first");
   if (n_bins < 0 || (hist && n_bins < 1)) return fail(CHYM_EINVAL, "bad n_bins");
@@ -476,6 +484,7 @@ chym_status chym_stats(chym_ctx* c, double E_gs, chym_stats_t* out, int64_t* hit
 }
 
 chym_status chym_get_state(chym_ctx* c, double* X_out, int64_t* k_out, void* stream) {
+  chym::TraceRange trace_("chym_get_state");
   if (!c || !X_out) return fail(CHYM_EINVAL, "NULL argument");
   if (c->prec < 0) return fail(CHYM_ESTATE, "no state");
   cudaStream_t st = (cudaStream_t)stream;
@@ -495,6 +504,7 @@ chym_status chym_get_state(chym_ctx* c, double* X_out, int64_t* k_out, void* str
 
 chym_status chym_set_state(chym_ctx* c, const double* X, int n_runs, const double* h, int n_h,
                            const uint64_t* seeds, int64_t k, int32_t prec, void* stream) {
+  chym::TraceRange trace_("chym_set_state");
   if (!c || !X || !h || !seeds) return fail(CHYM_EINVAL, "NULL argument");
   if (n_h < 1 || n_runs < 1 || n_runs % n_h) return fail(CHYM_EINVAL, "bad n_runs / n_h");
   if (k < 0) return fail(CHYM_EINVAL, "k must be >= 0");

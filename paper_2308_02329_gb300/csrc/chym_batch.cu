@@ -150,6 +150,7 @@ CHYM_API chym_status chym_batch_destroy(chym_batch* b) {
 CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
                                     const chym_schedule* schedules, int64_t steps,
                                     void* cuda_stream) {
+  chym::TraceRange trace_("chym_batch_run");
   if (!b || !params || !schedules) return fail(CHYM_EINVAL, "NULL argument");
   if (steps < 0) return fail(CHYM_EINVAL, "steps must be >= 0");
   const int n = (int)b->ctxs.size();
@@ -369,6 +370,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
 CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
                                      const chym_schedule* schedules, int64_t probe_steps,
                                      void* cuda_stream) {
+  chym::TraceRange trace_("chym_batch_tune");
   if (!b || !params || !schedules) return fail(CHYM_EINVAL, "NULL argument");
   if (probe_steps < 1) return fail(CHYM_EINVAL, "probe_steps must be >= 1");
   const int n = (int)b->ctxs.size();

@@ -7,6 +7,7 @@
 // (C -> alpha_mu C, text after Fig. 2 of arXiv 2308.02329).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,6 +127,17 @@ __host__ __device__ __forceinline__ double alpha_of(int kind, int64_t k, int64_t
   return a < 0.0 ? 0.0 : a;
 }
 
+}  // namespace chym
+
+namespace chym {
+// NVTX range over one ABI call, visible in Nsight Systems timelines; without an
+// attached tool the push and pop return at once.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 }  // namespace chym
 
 namespace chym {

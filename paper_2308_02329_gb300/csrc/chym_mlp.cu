@@ -458,6 +458,7 @@ CHYM_API chym_status chym_copy_state_device(chym_ctx* c, void* d_dst, void* stre
 
 CHYM_API chym_status chym_features_device(chym_ctx* c, const void* d_snapshot, double k_frac,
                                           float* d_features, void* stream) {
+  chym::TraceRange trace_("chym_features_device");
   if (!c || !d_snapshot || !d_features) return fail(CHYM_EINVAL, "NULL argument");
   if (c->prec < 0) return fail(CHYM_ESTATE, "no state");
   if (c->N > 4096) return fail(CHYM_EINVAL, "features need N <= 4096");
@@ -552,6 +553,7 @@ CHYM_API chym_status chym_mlp_get_params(chym_mlp* n, float* theta) {
 
 CHYM_API chym_status chym_mlp_forward_device(chym_mlp* n, const float* d_F, int B, float* d_logits,
                                              void* stream) {
+  chym::TraceRange trace_("chym_mlp_forward_device");
   if (!n || !d_F || !d_logits || B < 0) return fail(CHYM_EINVAL, "bad argument");
   if (B == 0) return CHYM_OK;
   const size_t smem = sizeof(SmemNet) + 8 * sizeof(WarpAct);
@@ -585,11 +587,13 @@ static chym_status mlp_grad_impl(chym_mlp* n, const float* d_F, const float* d_y
 
 CHYM_API chym_status chym_mlp_grad_device(chym_mlp* n, const float* d_F, const float* d_y, int B,
                                           float* d_grad_out, float* d_loss_out, void* stream) {
+  chym::TraceRange trace_("chym_mlp_grad_device");
   return mlp_grad_impl(n, d_F, d_y, B, 0.f, false, d_grad_out, d_loss_out, (cudaStream_t)stream);
 }
 
 CHYM_API chym_status chym_mlp_train_step_device(chym_mlp* n, const float* d_F, const float* d_y, int B,
                                                 float lr, float* d_loss_out, void* stream) {
+  chym::TraceRange trace_("chym_mlp_train_step_device");
   if (!(lr > 0.f)) return fail(CHYM_EINVAL, "lr must be > 0");
   return mlp_grad_impl(n, d_F, d_y, B, lr, true, nullptr, d_loss_out, (cudaStream_t)stream);
 }

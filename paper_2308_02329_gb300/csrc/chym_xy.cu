@@ -177,6 +177,7 @@ using namespace chym;
 extern "C" {
 
 CHYM_API chym_status chym_readout_xy_device(chym_ctx* c, double* d_E, uint64_t* d_spins, void* stream) {
+  chym::TraceRange trace_("chym_readout_xy_device");
   if (!c || !d_E) return fail(CHYM_EINVAL, "NULL argument");
   const chym_status ok = check_xy(c);
   if (ok != CHYM_OK) return ok;
@@ -185,6 +186,7 @@ CHYM_API chym_status chym_readout_xy_device(chym_ctx* c, double* d_E, uint64_t* 
 }
 
 CHYM_API chym_status chym_readout_xy(chym_ctx* c, double* E_out, uint64_t* spins_out, void* stream) {
+  chym::TraceRange trace_("chym_readout_xy");
   if (!c || !E_out) return fail(CHYM_EINVAL, "NULL argument");
   const chym_status ok = check_xy(c);
   if (ok != CHYM_OK) return ok;
