@@ -781,16 +781,18 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline_sample(w)
         # launches of our kernels per bench step: pump indices, init, energy and
-        # statistics per context; one persistent launch per dimension for the small-N
-        # contexts; the large-N path adds 3 layout kernels per context, one grouped GEMM
-        # launch per dimension and integration step, and one step-counter kernel per
-        # 16-step graph; FP32/FP64 contexts take one persistent SIMT launch each
+        # statistics per context (a pack of graphs: pump indices, init and one segment
+        # energy launch, its statistics are host-side); one persistent launch per
+        # dimension for the small-N contexts; the large-N path adds 3 layout kernels per
+        # context, one grouped GEMM launch per dimension and integration step, and one
+        # step-counter kernel per 16-step graph; FP32/FP64 contexts take one persistent
+        # SIMT launch each
         bf16 = prec == chym.PREC_BF16X2
         small = [j for j in jobs if j["N"] <= 128 and bf16]
         large = [j for j in jobs if j["N"] > 128 and bf16]
-        per_step = 4 * len(jobs) + len({j["D"] for j in small}) + 3 * len(large) + (
-            sim_steps * len({j["D"] for j in large}) + sim_steps // 16 if large else 0) + (
-            0 if bf16 else len(jobs))
+        per_step = sum(3 if "seg" in j else 4 for j in jobs) + len({j["D"] for j in small}) + \
+            3 * len(large) + (sim_steps * len({j["D"] for j in large}) + sim_steps // 16 if large else 0) + (
+                0 if bf16 else len(jobs))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
