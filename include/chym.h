@@ -18,7 +18,13 @@
  * continuous-time limit (gamma stands for beta b^2, kappa for the local
  * kappa L), with dimensional annealing C -> alpha_mu C (text after Fig. 2)
  * and additive Gaussian noise xi drawn from Philox4x32-10 (key = run seed,
- * counter = (p, tag << 8 | mu / 4, k lo, k hi), Box-Muller on the four words).
+ * Box-Muller on the four words of a block; for D >= 3 component mu of spin p
+ * takes normal mu mod 4 of the block with counter (p, tag << 8 | mu / 4, k lo,
+ * k hi); for D <= 2 the 4/D spins with the same p / (4/D) share the block with
+ * counter (p / (4/D), tag << 8, k lo, k hi) and spin p takes its normals
+ * (p mod 4/D) D + mu; tag 0 for the step noise, 1 for the initial state; k is
+ * the run's local step).  With per-spin coupling weights
+ * (chym_set_coupling_weights) the coupling term of spin p is eps w_p alpha_mu y.
  * The Ising readout is s_p = sign(x_{p,0}) (ties to +1) and the energy is
  * E = -sum_{p,q} J_pq s_p s_q (Eq. 3 with Ising spins).
  *
