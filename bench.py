@@ -18,7 +18,7 @@ with the learned early exit in continuous operation (finished and retired runs
 reseeded), each with its ground-state hits per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n100|sk1000|sk800]
-  python bench.py --impl reference ...   # the FP64 CPU checker on the host cores
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 Multi-GPU (torchrun): every rank runs its own replica of the workload with its
 own seeds (runs are independent, no collective on the data path); value = all
@@ -299,7 +299,7 @@ def oracle_jobs(w):
 
 
 def time_oracle(jobs, runs, steps, threads):
-    """Wall time of the FP64 checker: every job, `runs` runs x `steps` steps + energies."""
+    """Wall time of the FP64 oracle: every job, `runs` runs x `steps` steps + energies."""
     import oracle.oracle as O
     from paper_2308_02329_gb300 import inputs
     t0 = time.perf_counter()
@@ -314,7 +314,7 @@ def time_oracle(jobs, runs, steps, threads):
 
 
 def cpu_baseline_sample(w, target_s=10.0):
-    """The FP64 checker on a bounded sample of the same workload, on all host cores."""
+    """The FP64 oracle on a bounded sample of the same workload, on all host cores."""
     threads = os.cpu_count()
     jobs = oracle_jobs(w)
     runs = max(2 * threads, 16)
@@ -329,7 +329,7 @@ def cpu_baseline_sample(w, target_s=10.0):
 
 
 def run_reference(args, w, rank, world):
-    """The FP64 CPU checker as it stands, timed on the host cores on this workload."""
+    """The FP64 CPU oracle as it stands, timed on the host cores on this workload."""
     if rank != 0:
         return 0
     threads = os.cpu_count()
@@ -348,7 +348,7 @@ def run_reference(args, w, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(w, "fp64 (CPU checker)", w.steps),
+            "data": "synthetic", "config": workload_config(w, "fp64 (CPU oracle)", w.steps),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},

@@ -69,7 +69,7 @@ typedef enum {
 } chym_jkind;
 
 typedef enum {
-  CHYM_PREC_FP64 = 0,   /* FP64 state and arithmetic (checker-comparison mode) */
+  CHYM_PREC_FP64 = 0,   /* FP64 state and arithmetic (oracle-comparison mode) */
   CHYM_PREC_FP32 = 1,   /* FP32 state, FP32 SIMT coupling product (plain form) */
   CHYM_PREC_BF16X2 = 2  /* FP32 state; J x on tcgen05 tensor cores with J in BF16 and
                            x split into BF16 hi + lo, FP32 accumulation */

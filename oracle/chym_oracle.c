@@ -3,7 +3,7 @@
  * machine (CHYM) of "Hyperscaling in the coherent hyperspin machine"
  * (Calvanese Strinati & Conti, arXiv 2308.02329).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the independent checker that the
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent oracle that the
  * CUDA path is compared against.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline leg may build, load or call it.  It shares no code,
  * header, table or constant generator with the CUDA library.

@@ -1,4 +1,4 @@
-// chym_simt.cu -- SIMT step kernels (FP64 checker-comparison mode and the plain
+// chym_simt.cu -- SIMT step kernels (FP64 oracle-comparison mode and the plain
 // FP32 form) and the initial-state kernel.
 //
 // One CTA owns RC runs for the whole launch and keeps their state in shared

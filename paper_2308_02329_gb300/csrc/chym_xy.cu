@@ -6,7 +6,7 @@
 // u = (cos phi, sin phi): the pattern s_p = sign(x_p . u) changes only where u is
 // perpendicular to a spin, at phi_p = theta_p + pi/2 (mod pi), so sweeping phi
 // over [0, pi) flips one spin per critical angle.  One CTA per run:
-//   1. critical angles (FP64 atan2, so that their order matches the checker) and
+//   1. critical angles (FP64 atan2, so that their order matches the oracle) and
 //      the pattern of an axis inside the interval that wraps through pi;
 //   2. bitonic sort of (angle, spin) in shared memory;
 //   3. local fields h_q = sum_p J_qp s_p (N^2 multiply-adds) and E = -sum s h;

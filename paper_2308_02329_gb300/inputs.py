@@ -2,7 +2,7 @@
 
 This module holds no arithmetic of the method; it only draws the instances the
 paper's workloads are made of (random +-1 graphs, the Moebius ladder, Gaussian
-couplings) and the per-run seeds.  Both the CUDA path and the CPU checker take
+couplings) and the per-run seeds.  Both the CUDA path and the CPU oracle take
 their inputs from here.
 """
 import numpy as np

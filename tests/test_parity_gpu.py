@@ -1,4 +1,4 @@
-"""GPU parity of the CUDA path against the FP64 CPU checker, through the C ABI.
+"""GPU parity of the CUDA path against the FP64 CPU oracle, through the C ABI.
 
 Tolerances (written here, derived from the arithmetic):
   * FP64 mode: state and per-step right-hand side within 1e-10 relative;
@@ -58,7 +58,7 @@ FP64_CASES = [
 
 
 @pytest.mark.parametrize("N,D,n_h,reps,steps,graph", FP64_CASES)
-def test_fp64_state_matches_checker(N, D, n_h, reps, steps, graph):
+def test_fp64_state_matches_oracle(N, D, n_h, reps, steps, graph):
     ctx, J, X, Xo = _run_both(N, D, n_h, reps, steps, chym.PREC_FP64, graph)
     assert _rel_err(X, Xo) <= 1e-10
     ctx.close()
@@ -94,7 +94,7 @@ def test_fp64_one_step_rhs(D):
 
 
 @pytest.mark.parametrize("N,D,steps", [(20, 3, 60), (100, 4, 40), (64, 2, 50), (45, 8, 30)])
-def test_fp32_state_matches_checker(N, D, steps):
+def test_fp32_state_matches_oracle(N, D, steps):
     ctx, J, X, Xo = _run_both(N, D, 4, 5, steps, chym.PREC_FP32)
     assert _rel_err(X, Xo) <= 1e-4
     ctx.close()
@@ -145,7 +145,7 @@ def test_checkpoint_resume_is_bit_identical():
     b.close()
 
 
-def test_stats_match_checker_figures_of_merit():
+def test_stats_match_oracle_figures_of_merit():
     N, D, n_h, reps = 16, 2, 4, 16
     J, eps, h, seeds = make_case(N, D, n_h, reps, 5)
     ctx = chym.Context(J, D)
@@ -172,7 +172,7 @@ def test_stats_match_checker_figures_of_merit():
 
 def test_statistical_parity_fp64_full_horizon():
     """SK +-1 N=20, D=3, 8 pumps x 32 replicas, 3000 steps (1500 + 1500 annealing):
-    P_Ising(h) of the GPU and of the checker agree within binomial 95% intervals, and the
+    P_Ising(h) of the GPU and of the oracle agree within binomial 95% intervals, and the
     ground state is the brute-force one."""
     N, D, n_h, reps, K = 20, 3, 8, 32, 3000
     J, eps, h, seeds = make_case(N, D, n_h, reps, 0xC0FFEE)
@@ -227,7 +227,7 @@ def test_lambda_max_matches_eigvalsh():
         ctx.close()
 
 
-def test_ground_state_references_match_checker():
+def test_ground_state_references_match_oracle():
     for N, seed in ((8, 1), (14, 2), (20, 0xC0FFEE)):
         J = inputs.sk_pm1(N, seed)
         ctx = chym.Context(J, 1)
@@ -261,7 +261,7 @@ BF16_CASES = [
 
 
 @pytest.mark.parametrize("N,D,n_h,reps,steps,graph", BF16_CASES)
-def test_bf16x2_state_matches_checker(N, D, n_h, reps, steps, graph):
+def test_bf16x2_state_matches_oracle(N, D, n_h, reps, steps, graph):
     ctx, J, X, Xo = _run_both(N, D, n_h, reps, steps, chym.PREC_BF16X2, graph)
     assert np.all(np.isfinite(X))
     assert _rel_err(X, Xo) <= 1e-4
@@ -297,7 +297,7 @@ def test_bf16x2_energies_and_continuation():
 
 def test_bf16x2_full_size_launch_sampled_runs():
     """The benchmark's launch shape (N=100, D=4, 4096 runs = 32 h x 128 replicas):
-    sampled runs against the checker, run by run."""
+    sampled runs against the oracle, run by run."""
     N, D, n_h, reps, K = 100, 4, 32, 128, 150
     J, eps, h, seeds = make_case(N, D, n_h, reps, 0xC0FFEE + 1)
     ctx = chym.Context(J, D)
@@ -317,7 +317,7 @@ def test_bf16x2_full_size_launch_sampled_runs():
 def test_bf16x2_statistical_parity_long_horizon():
     """Moebius ladder N=100, D=4, 8 pumps x 32 replicas, 20000 steps (annealed over the
     second half): per-pump success probability and the mean energy above the exact
-    ground state agree with the FP64 checker within 95% intervals."""
+    ground state agree with the FP64 oracle within 95% intervals."""
     N, D, n_h, reps, K = 100, 4, 8, 32, 20000
     J, eps, h, seeds = make_case(N, D, n_h, reps, 5, graph="mobius")
     E_gs = O.ground_state_mobius(N, -1.0, -1.0)
@@ -346,8 +346,8 @@ def test_bf16x2_statistical_parity_long_horizon():
 @pytest.mark.parametrize("N,graph,prec", [(30, "sk", chym.PREC_BF16X2), (100, "mobius", chym.PREC_BF16X2),
                                           (150, "gauss", chym.PREC_BF16X2), (24, "sk", chym.PREC_FP64),
                                           (45, "sparse", chym.PREC_FP32), (257, "sk", chym.PREC_BF16X2)])
-def test_readout_xy_matches_checker(N, graph, prec):
-    """XY machine (D = 2, no annealing): the best-axis energies equal the checker's
+def test_readout_xy_matches_oracle(N, graph, prec):
+    """XY machine (D = 2, no annealing): the best-axis energies equal the oracle's
     rounding of the same final states (exactly for +-1 couplings), the returned
     spins reach them, and they are never above the first-component readout."""
     J, eps, h, seeds = make_case(N, 2, 2, 8, 21, graph)
@@ -401,7 +401,7 @@ K2_CASES = [
 
 
 @pytest.mark.parametrize("N,D,n_h,reps,steps,graph", K2_CASES)
-def test_large_n_state_matches_checker(N, D, n_h, reps, steps, graph):
+def test_large_n_state_matches_oracle(N, D, n_h, reps, steps, graph):
     ctx, J, X, Xo = _run_both(N, D, n_h, reps, steps, chym.PREC_BF16X2, graph)
     assert np.all(np.isfinite(X))
     assert _rel_err(X, Xo) <= 1e-4
@@ -432,7 +432,7 @@ def test_large_n_continuation_and_energies():
 @pytest.mark.parametrize("N,runs,steps", [(1000, 16384, 12), (800, 65536, 6)])
 def test_large_n_full_size_launch_sampled_runs(N, runs, steps):
     """Launch shapes of the dense SK workloads (N=1000 with 16384 runs, N=800 with
-    65536 runs, D=4): sampled runs against the checker, run by run."""
+    65536 runs, D=4): sampled runs against the oracle, run by run."""
     D, n_h = 4, 32
     reps = runs // n_h
     J, eps, h, seeds = make_case(N, D, n_h, reps, 0xC0FFEE + N)
@@ -494,9 +494,9 @@ def test_batch_equals_contexts_run_alone():
         b.close()
 
 
-def test_batch_many_small_instances_against_checker():
+def test_batch_many_small_instances_against_oracle():
     """Twenty uneven instances (N 50..128, D in {2,3,4,8}) in one batch; sampled runs
-    of each against the checker."""
+    of each against the oracle."""
     rng = np.random.default_rng(7)
     ctxs, prms, schs, meta = [], [], [], []
     K = 30
@@ -687,9 +687,9 @@ def test_diverged_runs_are_flagged_not_counted(N, D, prec):
 
 @pytest.mark.parametrize("D,prec,tol", [(2, chym.PREC_FP64, 1e-10), (1, chym.PREC_FP32, 1e-4),
                                         (2, chym.PREC_BF16X2, 1e-4), (3, chym.PREC_BF16X2, 1e-4)])
-def test_packed_graphs_match_checker(D, prec, tol):
+def test_packed_graphs_match_oracle(D, prec, tol):
     """Three sparse graphs packed into one context (block-diagonal J, per-spin coupling
-    weights 1/lambda_max of each graph): the state equals the checker's integration of
+    weights 1/lambda_max of each graph): the state equals the oracle's integration of
     J' = diag(w) J, and the segment energies equal each graph's own Ising energy of the
     same state (exact integers)."""
     from paper_2308_02329_gb300 import packing

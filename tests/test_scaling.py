@@ -72,8 +72,8 @@ def test_packing_plan_and_blocks():
     assert packing.spin_weights(P, [1.0, 2.0, 3.0]).tolist() == [1.0] * 30 + [2.0] * 7 + [3.0] * 12
 
 
-def test_host_figures_match_the_checker():
-    """The study's per-graph figures from run energies equal the checker's definitions,
+def test_host_figures_match_the_oracle():
+    """The study's per-graph figures from run energies equal the oracle's definitions,
     NaN (diverged) runs included."""
     rng = np.random.default_rng(5)
     for n_h, reps in ((7, 9), (1, 30), (21, 32)):
@@ -90,9 +90,9 @@ def test_host_figures_match_the_checker():
 @pytest.mark.gpu
 def test_small_study_matches_oracle_figures():
     """Both machines on 3 graphs of N = 8 and 12 each, all six packed into one context,
-    FP64: every graph's figures of merit equal the checker's figures from the checker's
+    FP64: every graph's figures of merit equal the oracle's figures from the oracle's
     own integration of the packed system (J' = diag(w) J with the per-graph weights), and
-    the exact ground states equal the checker's exhaustive search."""
+    the exact ground states equal the oracle's exhaustive search."""
     Ns, n_graphs, n_h, reps, steps = (8, 12), 3, 5, 8, 400
     graphs = SC.graphs_and_references(Ns, n_graphs)
     for (N, g, gseed, J, lam, E_gs, exact), (N2, g2, s2) in zip(graphs, SC.graph_set(Ns, n_graphs)):
