@@ -59,7 +59,7 @@ typedef enum {
   CHYM_ENOMEM = 2,   /* host or device allocation failed */
   CHYM_ECUDA = 3,    /* a CUDA call failed; chym_last_error() has the CUDA message */
   CHYM_ETIMEOUT = 4, /* a bounded device-side wait gave up */
-  CHYM_ENOTSUP = 5,  /* valid request that this build does not implement */
+  CHYM_ENOTSUP = 5,  /* valid request that the library does not implement */
   CHYM_ESTATE = 6    /* call out of order (e.g. energy before any run) */
 } chym_status;
 

@@ -146,7 +146,7 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
     if (e == cudaErrorInvalidConfiguration)
       return fail(CHYM_ENOTSUP, "problem too large for the selected kernel (N*D per run)");
     if (e == cudaErrorNotSupported)
-      return fail(CHYM_ENOTSUP, "no kernel for this precision and size in this build");
+      return fail(CHYM_ENOTSUP, "no kernel for this precision and size");
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     c->k += steps;
   }
