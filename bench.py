@@ -163,13 +163,13 @@ def workload_config(w, prec_name, sim_steps):
 
 
 def map_euler(lam, gain_rel):
-    """Euler form of one round trip (dt = 1) at gain K = K_th (1 + gain_rel): the
-    (dt, sigma, init_std, gamma, kappa, eps) tuple and the pump value h."""
-    a, d, beta = MAP_CAVITY["a"], MAP_CAVITY["d"], MAP_CAVITY["beta"]
-    b = 1.0 - a
-    K = (1.0 + gain_rel) / ((1.0 - d) * (a + b * lam))
-    g = (1.0 - d) * K
-    return (1.0, 1e-3, 0.1, g * b * b * beta * K * K, 0.0, g * b), g * a
+    """Euler form of one round trip (dt = 1) at gain K = K_th (1 + gain_rel), from the
+    package's reduction of the map: the (dt, sigma, init_std, gamma, kappa, eps) tuple
+    and the pump value h."""
+    from paper_2308_02329_gb300.round_trip import Cavity
+    cav = Cavity(**MAP_CAVITY)
+    prm, h = cav.euler((1.0 + gain_rel) * cav.threshold(lam), sigma=1e-3, init_std=0.1)
+    return (prm.dt, prm.sigma, prm.init_std, prm.gamma, prm.kappa, prm.eps), h
 
 
 def measured_peaks():
