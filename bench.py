@@ -373,10 +373,12 @@ def pack_jobs(jobs, lams, graphs, prec, torch):
             P = packing.build([graphs[items[i][0]["name"]] for i in members], list(range(len(members))))
             j0 = items[members[0]][0]
             ctx = chym.Context(P.J, j0["D"])
-            ctx.set_coupling_weights(packing.spin_weights(
-                P, [1.0 / items[i][1] if items[i][1] > 0 else 0.0 for i in members]))
+            lam = [items[i][1] for i in members]
+            if len(members) > 1:
+                ctx.set_coupling_weights(packing.spin_weights(P, [1.0 / l if l > 0 else 0.0 for l in lam]))
+            eps = EPS_HAT if len(members) > 1 else (EPS_HAT / lam[0] if lam[0] > 0 else 0.0)
             prm = chym.Params(dt=0.01, sigma=1e-3, init_std=0.1, gamma=j0["gamma"], kappa=j0["kappa"],
-                              eps=EPS_HAT, prec=prec)
+                              eps=eps, prec=prec)
             out.append(dict(j0, name=f"pack{k}_{mode}", N=P.N, ctx=ctx, prm=prm, seg=P.seg_begin,
                             members=[items[i][0]["name"] for i in members],
                             nnz=max(1, int((P.J != 0).sum(1).mean()))))

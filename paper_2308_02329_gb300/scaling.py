@@ -102,7 +102,7 @@ def pack_contexts(graphs, mode, n_h, reps, steps, eps_hat=0.5, prec=chym.PREC_BF
     blocks of a block-diagonal J when `pack` (each with its own eps_i through the
     per-spin coupling weights 1 / lambda_max(J_i)), initialised at step 0.  Returns
     a list of (context, params, schedule, packing.Pack, seeds, weights); the params'
-    eps is eps_hat."""
+    eps is eps_hat, or eps_hat / lambda_max with weights None for a graph alone."""
     m = MODES[mode]
     D = m["D"]
     h = inputs.pump_grid(1.0 - eps_hat, n_h)
@@ -113,8 +113,12 @@ def pack_contexts(graphs, mode, n_h, reps, steps, eps_hat=0.5, prec=chym.PREC_BF
         ctx = chym.Context(P.J, D)
         lam = [graphs[i][4] for i in members]
         w = packing.spin_weights(P, [1.0 / l if l > 0 else 0.0 for l in lam])
-        ctx.set_coupling_weights(w)
-        prm, sched = params_for(mode, 1.0, steps, eps_hat, prec)
+        if len(members) > 1:
+            ctx.set_coupling_weights(w)
+            prm, sched = params_for(mode, 1.0, steps, eps_hat, prec)
+        else:   # a graph alone (also one above 128 spins) needs no weights
+            w = None
+            prm, sched = params_for(mode, lam[0], steps, eps_hat, prec)
         seeds = inputs.run_seeds(graphs[members[0]][2], n_h * reps)
         ctx.run(prm, h, seeds, 0, sched, stream)
         out.append((ctx, prm, sched, P, seeds, w))

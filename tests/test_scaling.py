@@ -105,7 +105,8 @@ def test_small_study_matches_oracle_figures():
         assert len(jobs) == 1 and sorted(jobs[0][3].members) == list(range(len(graphs)))
         for ctx, prm, sched, P, seeds, w in jobs:
             ctx.close()
-            X = O.run(w[:, None] * P.J, SC.MODES[mode]["D"], inputs.h_per_run(inputs.pump_grid(0.5, n_h), reps),
+            Jp = P.J if w is None else w[:, None] * P.J
+            X = O.run(Jp, SC.MODES[mode]["D"], inputs.h_per_run(inputs.pump_grid(0.5, n_h), reps),
                       seeds, oracle_params(prm), oracle_schedule(sched), steps)
             for b, i in enumerate(P.members):
                 lo, hi = P.seg_begin[b], P.seg_begin[b + 1]
