@@ -120,3 +120,13 @@ def test_small_study_matches_oracle_figures():
     res = SC.study(Ns, n_graphs, steps, n_h=n_h, reps=reps)
     for mode in ("cim", "chym_da"):
         assert sorted(res[mode]["per_N"]) == list(Ns)
+
+
+@pytest.mark.gpu
+def test_study_with_graphs_above_one_tile():
+    """Graphs above 128 spins get a context each (no weights, large-N tensor-core path) and
+    mixed sizes pack around them; every graph gets its figures."""
+    rows = SC.run((150, 40, 90), "chym_da", 2, 3, 4, 120)
+    assert [(r.N, r.graph) for r in rows] == [(N, g) for N in (150, 40, 90) for g in range(2)]
+    for r in rows:
+        assert np.isfinite(r.E_gs) and 0.0 <= r.P_max <= 1.0 and len(r.hits_per_h) == 3
