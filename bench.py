@@ -82,6 +82,10 @@ WORKLOADS = {
     "fig4": Workload("fig4", "size scaling of Fig. 4: 20 % sparse +-1 graphs, N = 10..100, 16 graphs "
                      "per N; CIM (D=1, 51 h) and CHYM+DA (D=2 annealed, 21 h), 32 replicas, "
                      "20000 steps dt=0.01", [], (1, 2), 21, 32, 20000, compare_plain=False),
+    "sparse": Workload("sparse", "Moebius ladders N=2048 and N=4096, D=3, 2048 runs each "
+                       "(32 h x 64 replicas), 20000 steps dt=0.01: coupling over the nonzeros of J",
+                       [("moebius", "moebius", 2048), ("moebius4k", "moebius", 4096)], (3,), 32, 64, 20000,
+                       compare_plain=False),
     "map": Workload("map", "SK+-1 N=100, D=3, the cavity round-trip map of Eq. 1-2 (a=0.95, d=0.1, "
                     "beta=100), 32 gain values K = K_th (1 + dK), dK in [0, 0.25], 512 replicas "
                     "each (16384 runs), 20000 round trips", [("sk", "sk", 100)], (3,), 32, 512, 20000,
@@ -133,6 +137,8 @@ def build_graph(kind, N, rank, seed=None):
         return inputs.mobius_ladder(N)
     if kind == "sparse":
         return inputs.sparse_pm1(N, 0.2, seed)
+    if kind == "er1":
+        return inputs.sparse_pm1(N, 0.01, seed if seed is not None else INSTANCE_SEED + 3 + 1000 * rank)
     if kind == "sk":
         return inputs.sk_pm1(N, seed if seed is not None else INSTANCE_SEED + 1 + 1000 * rank)
     return inputs.gaussian(N, INSTANCE_SEED + 2 + 1000 * rank)
@@ -679,7 +685,7 @@ def main():
         ends = [fork.elapsed_time(e1) for _, e1 in marks]
         dur += (max(ends) - min(starts)) / 1e3
     peaks, peak_src = measured_peaks()
-    large = max(j["N"] for j in jobs) > 128 and prec == chym.PREC_BF16X2
+    large = any(j["N"] > 128 and not j["ctx"].uses_csr(prec) for j in jobs) and prec == chym.PREC_BF16X2
     if large:
         alg = args.steps * sum(2.0 * j["N"] ** 2 * j["D"] * j["runs"] * sim_steps for j in jobs)
         issued = args.steps * sum(
@@ -694,13 +700,14 @@ def main():
     else:
         on_alu = prec == chym.PREC_FP32
         alg = args.steps * sum(
-            alu_ops_per_element(j["D"], j["N"] if j["name"] == "sk" else j["nnz"], on_alu) *
+            alu_ops_per_element(j["D"], j["N"] if j["name"] == "sk" else j["nnz"], on_alu or j["ctx"].uses_csr(prec)) *
             j["N"] * j["D"] * j["runs"] * sim_steps for j in jobs)
         sm_mhz = clock_info.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * sm_mhz * 1e6
         roofline = {"bound": "alu", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
                     "unit": "Tlane-op/s", "frac": alg / dur / peak, "traffic": None,
-                    "kernel": "chym step kernel (" + args.prec + ")",
+                    "kernel": ("SIMT step kernel, coupling over the nonzeros of J (FP32)"
+                               if all(j["ctx"].uses_csr(prec) for j in jobs) else "chym step kernel (" + args.prec + ")"),
                     "peak_note": "152 SMs x 128 FP32 lanes x median SM clock during the region"}
 
     # ---------------- the plain FP32 form on the same workload ----------------
@@ -787,14 +794,15 @@ def main():
         # energy launch, its statistics are host-side); one persistent launch per
         # dimension for the small-N contexts; the large-N path adds 3 layout kernels per
         # context, one grouped GEMM launch per dimension and integration step, and one
-        # step-counter kernel per 16-step graph; FP32/FP64 contexts take one persistent
-        # SIMT launch each
+        # step-counter kernel per 16-step graph; FP32/FP64 contexts and sparse ones take
+        # one persistent SIMT launch each
         bf16 = prec == chym.PREC_BF16X2
         small = [j for j in jobs if j["N"] <= 128 and bf16]
-        large = [j for j in jobs if j["N"] > 128 and bf16]
+        large = [j for j in jobs if j["N"] > 128 and bf16 and not j["ctx"].uses_csr(prec)]
+        sparse = [j for j in jobs if j["ctx"].uses_csr(prec)]
         per_step = sum(3 if "seg" in j else 4 for j in jobs) + len({j["D"] for j in small}) + \
             3 * len(large) + (sim_steps * len({j["D"] for j in large}) + sim_steps // 16 if large else 0) + (
-                0 if bf16 else len(jobs))
+                len(sparse) if bf16 else len(jobs))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,

@@ -163,9 +163,20 @@ class Context:
         self.N = int(J.shape[0])
         self.D = int(D)
         self.kind = kind
+        # the library's rule (uses_csr in chym_internal.cuh): beyond one tensor-core tile
+        # (N > 128) a J with at most N^2 / 16 nonzeros runs its coupling product over the
+        # nonzeros on the CUDA cores in FP32/FP64, and in BF16 hi+lo mode only for
+        # N >= 1024, D >= 3 and at most N / 256 nonzeros per row
+        self.nnz = int(np.count_nonzero(J))
+        self.sparse = self.N > 128 and self.nnz * 16 <= self.N * self.N
+        self.csr_bf16 = self.sparse and self.N >= 1024 and self.D >= 3 and self.nnz * 256 <= self.N * self.N
         h = ctypes.c_void_p()
         _check(lib().chym_create(_ptr(J), self.N, self.D, int(kind), ctypes.byref(h)))
         self._h = h
+
+    def uses_csr(self, prec):
+        """Whether steps at precision prec run the coupling over the nonzeros of J."""
+        return self.sparse and (prec != PREC_BF16X2 or self.csr_bf16)
 
     def close(self):
         if getattr(self, "_h", None):

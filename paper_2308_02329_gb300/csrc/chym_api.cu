@@ -138,7 +138,7 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
     c->prec = prm->prec;
   }
   c->have_energy = false;
-  if (steps > 0 && c->d_w && c->N > 128 && c->prec == CHYM_PREC_BF16X2)
+  if (steps > 0 && c->d_w && c->N > 128 && c->prec == CHYM_PREC_BF16X2 && !uses_csr(c, c->prec))
     return fail(CHYM_ENOTSUP, "coupling weights need N <= 128 on the tensor-core path");
   if (steps > 0) {
     const StepConsts sc = make_step_consts(c, prm, sched, c->k, steps);
@@ -186,6 +186,8 @@ chym_status check_run_args(chym_ctx* c, const chym_params* prm, int n_h, int n_r
 }  // namespace
 
 cudaError_t launch_step(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStream_t st) {
+  // sparse J: the coupling over the nonzeros on the CUDA cores, FP32 state unless FP64
+  if (uses_csr(c, prec)) return launch_step_simt(c, sc, prec == CHYM_PREC_FP64 ? prec : CHYM_PREC_FP32, st);
   if (prec == CHYM_PREC_FP64 || prec == CHYM_PREC_FP32) return launch_step_simt(c, sc, prec, st);
   if (prec == CHYM_PREC_BF16X2)
     return c->N <= 128 ? launch_step_tc(c, sc, st) : launch_step_k2(c, sc, st);
@@ -244,6 +246,40 @@ chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J32, j32.data(), nn * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J8, j8.data(), nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+  // sparse J beyond one tensor-core tile: compressed rows for the CUDA-core product
+  size_t nz = 0;
+  for (size_t i = 0; i < nn; ++i) nz += J[i] != 0.0;
+  if (e == cudaSuccess && N > 128 && nz * 16 <= nn) {
+    std::vector<int32_t> rp(N + 1, 0), ci;
+    std::vector<float> v32;
+    std::vector<double> v64;
+    ci.reserve(nz);
+    v32.reserve(nz);
+    v64.reserve(nz);
+    for (int i = 0; i < N; ++i) {
+      for (int j = 0; j < N; ++j) {
+        const double v = J[(size_t)i * N + j];
+        if (v != 0.0) {
+          ci.push_back(j);
+          v32.push_back((float)v);
+          v64.push_back(v);
+        }
+      }
+      rp[i + 1] = (int32_t)ci.size();
+    }
+    c->sparse = true;
+    c->csr_bf16 = N >= 1024 && D >= 3 && nz * 256 <= nn;
+    c->nnz = (int)nz;
+    const size_t nzb = std::max<size_t>(nz, 1);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_rp, sizeof(int32_t) * (N + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ci, sizeof(int32_t) * nzb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_cv32, sizeof(float) * nzb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_cv64, sizeof(double) * nzb);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_rp, rp.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nz) e = cudaMemcpy(c->d_ci, ci.data(), sizeof(int32_t) * nz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nz) e = cudaMemcpy(c->d_cv32, v32.data(), sizeof(float) * nz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nz) e = cudaMemcpy(c->d_cv64, v64.data(), sizeof(double) * nz, cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     chym_status st = cuda_fail(e, "chym_create device setup");
     chym_destroy(c);
@@ -268,6 +304,10 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_spins);
   free_dev(c->d_w);
   free_dev(c->d_Eseg);
+  free_dev(c->d_rp);
+  free_dev(c->d_ci);
+  free_dev(c->d_cv32);
+  free_dev(c->d_cv64);
   free_dev(c->d_status);
   free_dev(c->d_scratch);
   free_dev(c->d_Ak2);

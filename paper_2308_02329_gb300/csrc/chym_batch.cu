@@ -164,7 +164,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
       return fail(CHYM_EINVAL, "bad params in the batch");
     if ((c->prec == CHYM_PREC_FP64) != (p.prec == CHYM_PREC_FP64))
       return fail(CHYM_EINVAL, "a context cannot change between FP64 and FP32 storage");
-    if (c->d_w && c->N > 128 && p.prec == CHYM_PREC_BF16X2)
+    if (c->d_w && c->N > 128 && p.prec == CHYM_PREC_BF16X2 && !uses_csr(c, p.prec))
       return fail(CHYM_ENOTSUP, "coupling weights need N <= 128 on the tensor-core path");
     if ((s.kind != 0 && s.kind != 1) || s.reserved != 0 ||
         (s.kind == 1 && (s.k_anneal < 0 || s.k_total <= s.k_anneal)))
@@ -200,7 +200,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   double small_total = total;
   for (int i = 0; i < n; ++i) {
     const chym_ctx* c = b->ctxs[i];
-    if (params[i].prec == CHYM_PREC_BF16X2 && c->N > 128)
+    if (params[i].prec == CHYM_PREC_BF16X2 && c->N > 128 && !uses_csr(c, params[i].prec))
       total += b->k2_cost * (double)k2_work_units(c->N, c->D, c->n_runs);
   }
   // SMs for the small-N dimensions (all of them when there is no large-N work)
@@ -295,7 +295,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     cudaStream_t s = b->streams[sidx];
     for (int i = 0; i < n; ++i) {
       chym_ctx* c = b->ctxs[i];
-      if (desc_of[i] >= 0 || params[i].prec != CHYM_PREC_BF16X2) continue;
+      if (desc_of[i] >= 0 || params[i].prec != CHYM_PREC_BF16X2 || uses_csr(c, params[i].prec)) continue;
       if (idx.empty()) CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
       c->prec = CHYM_PREC_BF16X2;
       descs.resize(descs.size() + kb);

@@ -166,6 +166,15 @@ struct chym_ctx {
   double* d_J64 = nullptr;    // FP64 N x N
   float* d_J32 = nullptr;     // FP32 N x N
   int8_t* d_J8 = nullptr;     // int8 N x N (+-1/0 couplings only)
+  // J in compressed rows when it is sparse (N > 128, at most N^2 / 16 nonzeros): the
+  // coupling product then runs on the CUDA cores over the nonzeros only
+  bool sparse = false;
+  bool csr_bf16 = false;      // the compressed rows also replace the BF16 tensor-core product
+  int nnz = 0;
+  int32_t* d_rp = nullptr;    // row starts, N + 1
+  int32_t* d_ci = nullptr;    // column of each nonzero
+  float* d_cv32 = nullptr;    // value of each nonzero, FP32 and FP64
+  double* d_cv64 = nullptr;
   void* d_Jbf16 = nullptr;    // BF16, padded for the tensor-core kernels (lazily built)
   int jbf16_ld = 0;           // leading dimension of d_Jbf16 in elements
   // batch
@@ -196,6 +205,13 @@ struct chym_ctx {
 };
 
 namespace chym {
+// Whether a step of context c at precision prec runs its coupling over the compressed
+// rows on the CUDA cores: always for a sparse J in FP32/FP64 (against the dense SIMT
+// product), and in place of the BF16 tensor-core product only where that measured
+// slower: N >= 1024, D >= 3 and at most N / 256 nonzeros per row.
+inline bool uses_csr(const chym_ctx* c, int32_t prec) {
+  return c->sparse && (prec != CHYM_PREC_BF16X2 || c->csr_bf16);
+}
 // kernel launchers (implemented in the .cu files)
 cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_std);
 cudaError_t launch_reseed(chym_ctx* c, const int32_t* d_runs, int n, const uint64_t* d_new_seeds,

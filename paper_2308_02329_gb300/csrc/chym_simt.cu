@@ -3,7 +3,9 @@
 //
 // One CTA owns RC runs for the whole launch and keeps their state in shared
 // memory across all steps; J (N x N) is staged in shared memory when it fits
-// and read through L1/L2 otherwise.  Per step:
+// and read through L1/L2 otherwise.  A sparse J (N > 128, at most N^2 / 16
+// nonzeros) is read as compressed rows instead, so the product costs 2 nnz D flops
+// per run and step rather than 2 N^2 D.  Per step:
 //   phase A  y_{p,mu} = sum_q J_pq x_{q,mu}  (C = J_N (x) 1_D, Eq. 1), J symmetric
 //            so thread p reads column p of row q (consecutive p: no bank conflict);
 //            each thread blocks RB runs so one J load feeds RB*D FMAs;
@@ -88,13 +90,21 @@ __global__ void init_kernel(T* __restrict__ X, const uint64_t* __restrict__ seed
   }
 }
 
-template <typename T, int D, bool J_SMEM>
+// Compressed rows of a sparse J: row p holds the nonzeros rp[p] .. rp[p + 1] - 1.
+template <typename T>
+struct CsrRows {
+  const int32_t* rp;
+  const int32_t* ci;
+  const T* cv;
+};
+
+template <typename T, int D, bool J_SMEM, bool CSR>
 __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg,
                                                         T* __restrict__ Xg,
                                                         const double* __restrict__ hg,
                                                         const uint64_t* __restrict__ seeds,
-                                                        StepConsts sc, int RC) {
-  constexpr int RB = SimtTraits<T>::RB;
+                                                        StepConsts sc, int RC, CsrRows<T> csr) {
+  constexpr int RB = CSR ? 1 : SimtTraits<T>::RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = sc.N;
   T* Js = reinterpret_cast<T*>(smem_raw);
@@ -124,12 +134,24 @@ __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) acc[b][mu] = T(0);
       const T* xg = Xs + (size_t)(g * RB) * N * D;
-      for (int q = 0; q < N; ++q) {
-        const T j = J_SMEM ? Jsrc[q * N + p] : __ldg(Jsrc + (size_t)q * N + p);
+      if constexpr (CSR) {
+        const int e1 = __ldg(csr.rp + p + 1);
+        for (int e = __ldg(csr.rp + p); e < e1; ++e) {
+          const T j = __ldg(csr.cv + e);
+          const int q = __ldg(csr.ci + e);
 #pragma unroll
-        for (int b = 0; b < RB; ++b)
+          for (int b = 0; b < RB; ++b)
 #pragma unroll
-          for (int mu = 0; mu < D; ++mu) acc[b][mu] = fma(j, xg[((size_t)b * N + q) * D + mu], acc[b][mu]);
+            for (int mu = 0; mu < D; ++mu) acc[b][mu] = fma(j, xg[((size_t)b * N + q) * D + mu], acc[b][mu]);
+        }
+      } else {
+        for (int q = 0; q < N; ++q) {
+          const T j = J_SMEM ? Jsrc[q * N + p] : __ldg(Jsrc + (size_t)q * N + p);
+#pragma unroll
+          for (int b = 0; b < RB; ++b)
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu) acc[b][mu] = fma(j, xg[((size_t)b * N + q) * D + mu], acc[b][mu]);
+        }
       }
 #pragma unroll
       for (int b = 0; b < RB; ++b)
@@ -170,11 +192,12 @@ __global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg
 
 template <typename T, int D>
 cudaError_t launch_simt_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
-  constexpr int RB = SimtTraits<T>::RB;
+  const bool csr = c->sparse;  // the SIMT kernels use the compressed rows whenever they exist
+  const int RB = csr ? 1 : SimtTraits<T>::RB;
   const int N = c->N;
   const size_t budget = 200 * 1024;
   const size_t j_bytes = (size_t)N * N * sizeof(T);
-  const bool j_smem = j_bytes <= budget / 2;
+  const bool j_smem = !csr && j_bytes <= budget / 2;
   const size_t per_run = (size_t)2 * N * D * sizeof(T);
   const size_t avail = budget - (j_smem ? j_bytes : 0);
   int RC = (int)std::min<size_t>(avail / per_run, 64);
@@ -189,17 +212,12 @@ cudaError_t launch_simt_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st
   const int grid = (sc.n_runs + RC - 1) / RC;
   const T* J = sizeof(T) == 8 ? (const T*)c->d_J64 : (const T*)c->d_J32;
   T* X = (T*)c->d_X;
-  if (j_smem) {
-    auto kern = step_simt_kernel<T, D, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, threads, smem, st>>>(J, X, c->d_h, c->d_seeds, sc, RC);
-  } else {
-    auto kern = step_simt_kernel<T, D, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, threads, smem, st>>>(J, X, c->d_h, c->d_seeds, sc, RC);
-  }
+  const CsrRows<T> rows{c->d_rp, c->d_ci, sizeof(T) == 8 ? (const T*)c->d_cv64 : (const T*)c->d_cv32};
+  auto kern = csr ? step_simt_kernel<T, D, false, true>
+                  : j_smem ? step_simt_kernel<T, D, true, false> : step_simt_kernel<T, D, false, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, threads, smem, st>>>(J, X, c->d_h, c->d_seeds, sc, RC, rows);
   return cudaGetLastError();
 }
 

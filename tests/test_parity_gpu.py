@@ -736,3 +736,66 @@ def test_coupling_weights_arguments():
         with pytest.raises(chym.ChymError):
             ctx.energy_segments(bad)
     ctx.close()
+
+
+def _sparse_graph(kind, N, seed):
+    return inputs.mobius_ladder(N) if kind == "mobius" else inputs.sparse_pm1(N, 0.02, seed)
+
+
+@pytest.mark.parametrize("N,D,graph,prec,tol,csr", [(200, 3, "mobius", chym.PREC_FP64, 1e-10, True),
+                                                    (200, 2, "mobius", chym.PREC_FP32, 1e-4, True),
+                                                    (300, 4, "er2", chym.PREC_FP32, 1e-4, True),
+                                                    (260, 1, "mobius", chym.PREC_FP64, 1e-10, True),
+                                                    (1024, 3, "mobius", chym.PREC_BF16X2, 1e-4, True),
+                                                    (410, 2, "er2", chym.PREC_BF16X2, 1e-4, False)])
+def test_sparse_graphs_match_oracle(N, D, graph, prec, tol, csr):
+    """Sparse J beyond one tile (the Moebius ladder, 2 % Erdos-Renyi graphs): in FP32/FP64,
+    and in BF16 mode for the very sparse large ones, the product runs over the nonzeros on
+    the CUDA cores (elsewhere on the tensor cores); states match the oracle's dense
+    integration, energies exactly."""
+    J = _sparse_graph(graph, N, 77 + N)
+    ctx = chym.Context(J, D)
+    assert ctx.sparse and ctx.uses_csr(prec) == csr
+    n_h, reps, steps = 3, 5, 60
+    h = inputs.pump_grid(0.5, n_h)
+    seeds = inputs.run_seeds(5 + N, n_h * reps)
+    prm = chym.Params(eps=0.5 / ctx.lambda_max(), prec=prec)
+    sch = chym.Schedule(1, steps // 2, steps)
+    ctx.run(prm, h, seeds, steps, sch)
+    X, k = ctx.get_state()
+    assert k == steps
+    Xo = O.run(J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm), oracle_schedule(sch), steps)
+    assert _rel_err(X, Xo) <= tol
+    E = ctx.energy()
+    assert np.array_equal(E, O.ising_energies(J, O.readout(X)))
+    ctx.close()
+
+
+def test_batch_with_sparse_dense_and_small_contexts_equals_them_alone():
+    """A batch mixing a sparse large context (CUDA-core product), a dense large one (the
+    persistent tensor-core kernel) and a small one gives each the states it has alone."""
+    specs = [(inputs.mobius_ladder(1024), 3), (inputs.sk_pm1(200, 9), 2), (inputs.sk_pm1(64, 10), 4)]
+    steps = 48
+
+    def make():
+        out = []
+        for k, (J, D) in enumerate(specs):
+            c = chym.Context(J, D)
+            prm = chym.Params(eps=0.5 / c.lambda_max(), prec=chym.PREC_BF16X2)
+            sch = chym.Schedule(1, 20, 60)
+            c.run(prm, inputs.pump_grid(0.5, 2), inputs.run_seeds(31 + k, 12), 0, sch)
+            out.append((c, prm, sch))
+        return out
+
+    batched = make()
+    assert [c.uses_csr(p.prec) for c, p, _ in batched] == [True, False, False]
+    b = chym.Batch([c for c, _, _ in batched])
+    b.run([p for _, p, _ in batched], [s for _, _, s in batched], steps)
+    b.status()
+    b.close()
+    alone = make()
+    for (c, p, s), (ca, _, _) in zip(alone, batched):
+        c.run(p, None, None, steps, s)
+        assert np.array_equal(c.get_state()[0], ca.get_state()[0])
+        c.close()
+        ca.close()
