@@ -72,7 +72,8 @@ typedef enum {
   CHYM_PREC_FP64 = 0,   /* FP64 state and arithmetic (oracle-comparison mode) */
   CHYM_PREC_FP32 = 1,   /* FP32 state, FP32 SIMT coupling product (plain form) */
   CHYM_PREC_BF16X2 = 2  /* FP32 state; J x on tcgen05 tensor cores with J in BF16 and
-                           x split into BF16 hi + lo, FP32 accumulation */
+                           x split into BF16 hi + lo, FP32 accumulation (FP32 over
+                           the nonzeros for very sparse large J, see chym_create) */
 } chym_prec;
 
 typedef struct {
@@ -112,7 +113,11 @@ CHYM_API const char* chym_last_error(void);
  * (J_N is the symmetric adjacency matrix of the graph, text after Eq. 1);
  * kind CHYM_J_PM1 additionally requires entries in {-1,0,1}.
  * Limits: 1 <= N <= 4096, 1 <= D <= 8.  EINVAL otherwise; ECUDA/ENOMEM on
- * device failures.  *out is set only on success. */
+ * device failures.  *out is set only on success.  For N > 128 and at most N^2/16
+ * nonzeros the context also keeps J in compressed rows: steps in FP32/FP64 then sum
+ * the coupling over the nonzeros on the CUDA cores, and so do steps in BF16X2 mode
+ * when N >= 1024, D >= 3 and J has at most N/256 nonzeros per row (where that was
+ * measured faster than the tensor-core product); the state stays FP32 there. */
 CHYM_API chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx** out);
 
 /* Release every device and host resource of ctx (NULL is accepted). */
