@@ -99,7 +99,7 @@ struct CsrRows {
 };
 
 template <typename T, int D, bool J_SMEM, bool CSR>
-__global__ void __launch_bounds__(512) step_simt_kernel(const T* __restrict__ Jg,
+__global__ void __launch_bounds__(CSR && sizeof(T) == 4 ? 1024 : 512) step_simt_kernel(const T* __restrict__ Jg,
                                                         T* __restrict__ Xg,
                                                         const double* __restrict__ hg,
                                                         const uint64_t* __restrict__ seeds,
@@ -208,7 +208,8 @@ cudaError_t launch_simt_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   while (RC > RB && (int64_t)((sc.n_runs + RC - 1) / RC) < sms) RC -= RB;
   const size_t smem = (j_smem ? j_bytes : 0) + (size_t)RC * per_run;
-  const int threads = std::min(512, std::max(64, ((N * (RC / RB) + 31) / 32) * 32));
+  // the FP32 compressed-row form needs few registers: twice the warps hide its gathers
+  const int threads = std::min(csr && sizeof(T) == 4 ? 1024 : 512, std::max(64, ((N * (RC / RB) + 31) / 32) * 32));
   const int grid = (sc.n_runs + RC - 1) / RC;
   const T* J = sizeof(T) == 8 ? (const T*)c->d_J64 : (const T*)c->d_J32;
   T* X = (T*)c->d_X;
