@@ -113,11 +113,13 @@ CHYM_API const char* chym_last_error(void);
  * (J_N is the symmetric adjacency matrix of the graph, text after Eq. 1);
  * kind CHYM_J_PM1 additionally requires entries in {-1,0,1}.
  * Limits: 1 <= N <= 4096, 1 <= D <= 8.  EINVAL otherwise; ECUDA/ENOMEM on
- * device failures.  *out is set only on success.  For N > 128 and at most N^2/16
- * nonzeros the context also keeps J in compressed rows: steps in FP32/FP64 then sum
- * the coupling over the nonzeros on the CUDA cores, and so do steps in BF16X2 mode
- * when N >= 1024, D >= 3 and J has at most N/256 nonzeros per row (where that was
- * measured faster than the tensor-core product); the state stays FP32 there. */
+ * device failures.  *out is set only on success.  With at most N^2/16 nonzeros
+ * the context also keeps J in compressed rows: steps in FP32/FP64 then sum the
+ * coupling over the nonzeros on the CUDA cores, and so do steps in BF16X2 mode when
+ * N >= 1024, D >= 3, J has on average at most N/256 nonzeros per row
+ * (nnz <= N^2/256; where that was measured faster than the tensor-core product) and
+ * 2 N D floats fit the SIMT kernel's 200 KiB of shared memory; the state stays FP32
+ * there. */
 CHYM_API chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx** out);
 
 /* Release every device and host resource of ctx (NULL is accepted). */

@@ -302,6 +302,64 @@ double oracle_hyperspin_energy(const double* J, int N, int D, const double* x) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* XY ground state (the reference of the XY machine, D = 2 without           */
+/* annealing: the text after Fig. 2 and its footnote compare the machine's    */
+/* energy with the XY ground state found by a numerical minimiser).  Planar   */
+/* unit spins sigma_p = (cos theta_p, sin theta_p) turn Eq. 3 into            */
+/*   E_XY(theta) = - sum_{p,q} J_pq cos(theta_p - theta_q).                   */
+/* The terms that hold theta_p are -2 sum_q J_pq cos(theta_p - theta_q)       */
+/* (J symmetric), i.e. minus twice the projection of sigma_p on the local     */
+/* field f_p = sum_q J_pq sigma_q; with the others fixed the exact minimiser  */
+/* over theta_p is the direction of f_p (kept when f_p = 0).  Coordinate      */
+/* descent sweeps p = 0..N-1 with that update; each update can only lower E,  */
+/* and a sweep that lowers E by at most tol |E| (or max_sweeps sweeps) ends a  */
+/* start.  n_starts starts from the given initial angles theta0[start][p]     */
+/* (drawn by the caller); the lowest energy is returned and its angles written */
+/* to theta_out (nullable).  An upper bound on the true XY ground-state       */
+/* energy, equal to it when one of the starts reaches the global minimum.     */
+/* ------------------------------------------------------------------------ */
+static double xy_energy(const double* J, int N, const double* th) {
+  double e = 0.0;
+  for (int p = 0; p < N; ++p)
+    for (int q = 0; q < N; ++q) e += J[(size_t)p * N + q] * cos(th[p] - th[q]);
+  return -e;
+}
+
+double oracle_xy_energy(const double* J, int N, const double* theta) {
+  return xy_energy(J, N, theta);
+}
+
+double oracle_xy_ground_state(const double* J, int N, int n_starts, const double* theta0,
+                              int max_sweeps, double tol, double* theta_out) {
+  double best = INFINITY;
+  double* th = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+  for (int st = 0; st < n_starts; ++st) {
+    memcpy(th, theta0 + (size_t)st * N, sizeof(double) * (size_t)N);
+    double e = xy_energy(J, N, th);
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      for (int p = 0; p < N; ++p) {
+        double fx = 0.0, fy = 0.0;
+        for (int q = 0; q < N; ++q) {
+          fx += J[(size_t)p * N + q] * cos(th[q]);
+          fy += J[(size_t)p * N + q] * sin(th[q]);
+        }
+        if (fx != 0.0 || fy != 0.0) th[p] = atan2(fy, fx);
+      }
+      const double e_new = xy_energy(J, N, th);
+      const double drop = e - e_new;
+      e = e_new;
+      if (drop <= tol * fabs(e)) break;
+    }
+    if (e < best) {
+      best = e;
+      if (theta_out) memcpy(theta_out, th, sizeof(double) * (size_t)N);
+    }
+  }
+  free(th);
+  return best;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Ising ground state by exhaustive enumeration (the reference the paper's   */
 /* success probability is measured against).  The global flip s -> -s keeps */
 /* E, so s_{N-1} = +1 is fixed and the 2^{N-1} others are walked in Gray-code */

@@ -55,6 +55,11 @@ def _L():
         lib.oracle_ground_state_mobius.argtypes = [ctypes.c_int, ctypes.c_double,
                                                    ctypes.c_double]
         lib.oracle_ground_state_mobius.restype = ctypes.c_double
+        lib.oracle_xy_energy.argtypes = [dp, ctypes.c_int, dp]
+        lib.oracle_xy_energy.restype = ctypes.c_double
+        lib.oracle_xy_ground_state.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
+                                               ctypes.c_double, dp]
+        lib.oracle_xy_ground_state.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -199,3 +204,25 @@ def ground_state_bruteforce(J):
 
 def ground_state_mobius(N, Jr=-1.0, Jg=-1.0):
     return _L().oracle_ground_state_mobius(int(N), float(Jr), float(Jg))
+
+
+def xy_energy(J, theta):
+    """E_XY = -sum_{p,q} J_pq cos(theta_p - theta_q): Eq. 3 with planar unit spins."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    return _L().oracle_xy_energy(_p(J, ctypes.c_double), J.shape[0], _p(th, ctypes.c_double))
+
+
+def xy_ground_state(J, n_starts=64, seed=0, max_sweeps=20000, tol=1e-14):
+    """XY ground-state energy (the reference of the XY machine, text after Fig. 2 and its
+    footnote) by multi-start coordinate descent on the angles: n_starts starts from angles
+    drawn uniformly on [0, 2 pi) by numpy's PCG64 with `seed`.  Returns (energy, angles)."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    N = J.shape[0]
+    th0 = np.random.default_rng(seed).uniform(0.0, 2.0 * np.pi, size=(n_starts, N))
+    th0 = np.ascontiguousarray(th0)
+    out = np.zeros(N, dtype=np.float64)
+    e = _L().oracle_xy_ground_state(_p(J, ctypes.c_double), N, int(n_starts),
+                                    _p(th0, ctypes.c_double), int(max_sweeps), float(tol),
+                                    _p(out, ctypes.c_double))
+    return e, out

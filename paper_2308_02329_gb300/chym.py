@@ -163,13 +163,16 @@ class Context:
         self.N = int(J.shape[0])
         self.D = int(D)
         self.kind = kind
-        # the library's rule (uses_csr in chym_internal.cuh): beyond one tensor-core tile
-        # (N > 128) a J with at most N^2 / 16 nonzeros runs its coupling product over the
-        # nonzeros on the CUDA cores in FP32/FP64, and in BF16 hi+lo mode only for
-        # N >= 1024, D >= 3 and at most N / 256 nonzeros per row
+        # the library's rule (uses_csr in chym_internal.cuh): a J with at most N^2 / 16
+        # nonzeros runs its coupling product over the nonzeros on the CUDA cores in
+        # FP32/FP64, and in BF16 hi+lo mode only for N >= 1024, D >= 3, on average at most
+        # N / 256 nonzeros per row, and a run state (2 N D floats) within the SIMT
+        # kernel's 200 KiB of shared memory
         self.nnz = int(np.count_nonzero(J))
-        self.sparse = self.N > 128 and self.nnz * 16 <= self.N * self.N
-        self.csr_bf16 = self.sparse and self.N >= 1024 and self.D >= 3 and self.nnz * 256 <= self.N * self.N
+        self.sparse = self.nnz * 16 <= self.N * self.N
+        self.csr_bf16 = (self.sparse and self.N >= 1024 and self.D >= 3
+                         and self.nnz * 256 <= self.N * self.N
+                         and 2 * self.N * self.D * 4 <= 200 * 1024)
         h = ctypes.c_void_p()
         _check(lib().chym_create(_ptr(J), self.N, self.D, int(kind), ctypes.byref(h)))
         self._h = h
@@ -450,17 +453,20 @@ class Batch:
             pass
 
 
-def stats_noalloc(d_E, n_runs, n_h, kind, E_gs, n_bins=0, stream=0):
+def stats_noalloc(d_E, n_runs, n_h, kind, E_gs, n_bins=0, stream=0, with_hits=True):
     """Figures of merit from device energies d_E (a device address) without any device
-    allocation by the library (see chym_stats_noalloc in include/chym.h)."""
+    allocation by the library (see chym_stats_noalloc in include/chym.h).  With
+    with_hits=False no per-pump buffer is passed (the library then reads the counts it
+    needs into its own host array) and the result has no "hits" entry."""
     st = CStats()
-    hits = np.zeros(n_h, dtype=np.int64)
+    hits = np.zeros(n_h, dtype=np.int64) if with_hits else None
     hist = np.zeros(n_bins, dtype=np.int64) if n_bins else None
     _check(lib().chym_stats_noalloc(ctypes.c_void_p(d_E), int(n_runs), int(n_h), int(kind),
                                     float(E_gs), ctypes.byref(st), _ptr(hits), _ptr(hist),
                                     int(n_bins), ctypes.c_void_p(stream)))
     out = {f: getattr(st, f) for f, _ in CStats._fields_}
-    out["hits"] = hits
+    if hits is not None:
+        out["hits"] = hits
     if hist is not None:
         out["hist"] = hist
     return out

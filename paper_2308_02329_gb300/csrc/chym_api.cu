@@ -246,10 +246,10 @@ chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J32, j32.data(), nn * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J8, j8.data(), nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
-  // sparse J beyond one tensor-core tile: compressed rows for the CUDA-core product
+  // sparse J: compressed rows for the CUDA-core product
   size_t nz = 0;
   for (size_t i = 0; i < nn; ++i) nz += J[i] != 0.0;
-  if (e == cudaSuccess && N > 128 && nz * 16 <= nn) {
+  if (e == cudaSuccess && nz * 16 <= nn) {
     std::vector<int32_t> rp(N + 1, 0), ci;
     std::vector<float> v32;
     std::vector<double> v64;
@@ -268,7 +268,8 @@ chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx
       rp[i + 1] = (int32_t)ci.size();
     }
     c->sparse = true;
-    c->csr_bf16 = N >= 1024 && D >= 3 && nz * 256 <= nn;
+    c->csr_bf16 = N >= 1024 && D >= 3 && nz * 256 <= nn &&
+                  (size_t)2 * N * D * sizeof(float) <= kSimtSmemBudget;
     c->nnz = (int)nz;
     const size_t nzb = std::max<size_t>(nz, 1);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_rp, sizeof(int32_t) * (N + 1));

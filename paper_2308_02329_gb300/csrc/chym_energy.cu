@@ -341,12 +341,12 @@ extern "C" CHYM_API chym_status chym_stats_noalloc(const double* d_E, int n_runs
   StatsOut head;
   CHYM_CUDA_TRY(cudaMemcpyAsync(&head, scratch, sizeof(head), cudaMemcpyDeviceToHost, st));
   const long long* d_hits = reinterpret_cast<const long long*>((const StatsOut*)scratch + 1);
-  long long hits_small[64];
-  long long* hits = hits_per_h ? reinterpret_cast<long long*>(hits_per_h) : nullptr;
-  const bool need_tmp = !hits;
-  // per-pump counts are needed for P_max and W; without a caller buffer they are
-  // read in slices of 64 into the stack
-  if (hits) CHYM_CUDA_TRY(cudaMemcpyAsync(hits, d_hits, sizeof(long long) * n_h, cudaMemcpyDeviceToHost, st));
+  // per-pump counts are needed for P_max and W; without a caller buffer they go to a
+  // fixed per-thread host array of the maximum size.  Every copy is ordered on st and
+  // one synchronisation of st ends the call, so no other stream is waited for.
+  static thread_local long long hits_tmp[kNoAllocMaxH];
+  long long* hits = hits_per_h ? reinterpret_cast<long long*>(hits_per_h) : hits_tmp;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(hits, d_hits, sizeof(long long) * n_h, cudaMemcpyDeviceToHost, st));
   if (hist && n_bins)
     CHYM_CUDA_TRY(cudaMemcpyAsync(hist, d_hits + n_h, sizeof(long long) * n_bins,
                                   cudaMemcpyDeviceToHost, st));
@@ -354,18 +354,11 @@ extern "C" CHYM_API chym_status chym_stats_noalloc(const double* d_E, int n_runs
   const int reps = n_runs / n_h;
   double pmax = 0.0, psum = 0.0;
   int nz = 0;
-  for (int i0 = 0; i0 < n_h; i0 += 64) {
-    const int cnt = std::min(64, n_h - i0);
-    const long long* hv = need_tmp ? hits_small : hits + i0;
-    if (need_tmp) {
-      CHYM_CUDA_TRY(cudaMemcpy(hits_small, d_hits + i0, sizeof(long long) * cnt, cudaMemcpyDeviceToHost));
-    }
-    for (int i = 0; i < cnt; ++i) {
-      const double P = (double)hv[i] / reps;
-      pmax = std::max(pmax, P);
-      psum += P;
-      if (hv[i] > 0) ++nz;
-    }
+  for (int i = 0; i < n_h; ++i) {
+    const double P = (double)hits[i] / reps;
+    pmax = std::max(pmax, P);
+    psum += P;
+    if (hits[i] > 0) ++nz;
   }
   out->P_max = pmax;
   out->W_range = nz ? psum / nz : 0.0;

@@ -52,6 +52,10 @@ struct SegTable {
   int begin[kMaxSegments + 1];
 };
 
+// Shared-memory budget of the SIMT step kernels, which keep every run of a CTA in
+// shared memory for a whole launch (state and coupling product: 2 N D values a run).
+constexpr size_t kSimtSmemBudget = 200 * 1024;
+
 // Device status word: bit flags raised by kernels, read back by the host.
 enum : unsigned { STATUS_TIMEOUT = 1u, STATUS_BAD_LAUNCH = 2u };
 
@@ -166,8 +170,8 @@ struct chym_ctx {
   double* d_J64 = nullptr;    // FP64 N x N
   float* d_J32 = nullptr;     // FP32 N x N
   int8_t* d_J8 = nullptr;     // int8 N x N (+-1/0 couplings only)
-  // J in compressed rows when it is sparse (N > 128, at most N^2 / 16 nonzeros): the
-  // coupling product then runs on the CUDA cores over the nonzeros only
+  // J in compressed rows when it is sparse (at most N^2 / 16 nonzeros): the coupling
+  // product then runs on the CUDA cores over the nonzeros only
   bool sparse = false;
   bool csr_bf16 = false;      // the compressed rows also replace the BF16 tensor-core product
   int nnz = 0;
@@ -208,7 +212,9 @@ namespace chym {
 // Whether a step of context c at precision prec runs its coupling over the compressed
 // rows on the CUDA cores: always for a sparse J in FP32/FP64 (against the dense SIMT
 // product), and in place of the BF16 tensor-core product only where that measured
-// slower: N >= 1024, D >= 3 and at most N / 256 nonzeros per row.
+// slower and a run's state fits the SIMT kernel's shared memory: N >= 1024, D >= 3,
+// on average at most N / 256 nonzeros per row (nnz <= N^2 / 256) and
+// 2 N D sizeof(float) <= kSimtSmemBudget.
 inline bool uses_csr(const chym_ctx* c, int32_t prec) {
   return c->sparse && (prec != CHYM_PREC_BF16X2 || c->csr_bf16);
 }

@@ -195,7 +195,7 @@ cudaError_t launch_simt_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st
   const bool csr = c->sparse;  // the SIMT kernels use the compressed rows whenever they exist
   const int RB = csr ? 1 : SimtTraits<T>::RB;
   const int N = c->N;
-  const size_t budget = 200 * 1024;
+  const size_t budget = kSimtSmemBudget;
   const size_t j_bytes = (size_t)N * N * sizeof(T);
   const bool j_smem = !csr && j_bytes <= budget / 2;
   const size_t per_run = (size_t)2 * N * D * sizeof(T);

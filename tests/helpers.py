@@ -32,3 +32,17 @@ def oracle_params(p):
 
 def oracle_schedule(s):
     return O.Schedule(kind=s.kind, k_anneal=s.k_anneal, k_total=s.k_total)
+
+
+def rel_err(a, b):
+    """Largest |a - b| relative to the scale of its own (run, component): for states laid
+    out X[run, p, mu] the scale is max_p |b[run, :, mu]|, floored at 1e-12 of the whole
+    array's scale, so that the components annealing drives towards zero are held to the
+    same relative tolerance as the surviving one.  Other shapes: max |a - b| / max |b|."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    glob = max(float(np.max(np.abs(b))) if b.size else 0.0, 1e-300)
+    if b.ndim == 3 and b.size:
+        scale = np.maximum(np.max(np.abs(b), axis=1, keepdims=True), 1e-12 * glob)
+        return float(np.max(np.abs(a - b) / scale))
+    return float(np.max(np.abs(a - b))) / glob if b.size else 0.0

@@ -393,3 +393,76 @@ def test_round_xy_invariances():
     z[4] = 0.0
     ez, sz = O.round_xy(J, z)
     assert sz[4] == 1 and O.ising_energy(J, sz) == ez
+
+
+# --------------------------------------------------------------------------
+# XY ground state (reference of the XY machine, D = 2 without annealing)
+# --------------------------------------------------------------------------
+def _ring(N, j):
+    J = np.zeros((N, N))
+    for i in range(N):
+        J[i, (i + 1) % N] = J[(i + 1) % N, i] = j
+    return J
+
+
+def test_xy_ground_state_closed_forms():
+    """Closed forms of the XY ground state in the full double-sum convention of Eq. 3:
+    a ferromagnet aligns every spin (E = -N(N-1)); an antiferromagnetic ring of odd N
+    cannot alternate, and its best compromise turns each bond by pi - pi/N
+    (E = -2N cos(pi/N)); an even antiferromagnetic ring alternates (E = -2N)."""
+    for N in (2, 5, 10):
+        J = np.ones((N, N)) - np.eye(N)
+        assert O.xy_ground_state(J, n_starts=8)[0] == pytest.approx(-N * (N - 1), rel=1e-12)
+    for N in (3, 5, 7, 9, 15):
+        e, th = O.xy_ground_state(_ring(N, -1.0), n_starts=16)
+        assert e == pytest.approx(-2 * N * np.cos(np.pi / N), rel=1e-10)
+        assert O.xy_energy(_ring(N, -1.0), th) == pytest.approx(e, rel=1e-14)
+    for N in (4, 8, 12):
+        assert O.xy_ground_state(_ring(N, -1.0), n_starts=16)[0] == pytest.approx(-2 * N, rel=1e-10)
+    # a ferromagnetic ring and the AF triangle (-3 against the Ising -2)
+    assert O.xy_ground_state(_ring(6, 1.0), n_starts=4)[0] == pytest.approx(-12, rel=1e-12)
+    assert O.xy_ground_state(_ring(3, -1.0), n_starts=4)[0] == pytest.approx(-3, rel=1e-10)
+
+
+def test_xy_ground_state_bounds_the_ising_one():
+    """XY spins include the Ising states (theta in {0, pi}), so E_XY,GS <= E_Ising,GS, with
+    equality on an unfrustrated graph (a gauge transform tau_p tau_q |J_pq| of a
+    ferromagnet, whose Ising and XY ground states both reach -sum |J|)."""
+    for seed in range(4):
+        for J in (inputs.sk_pm1(12, 40 + seed), inputs.sparse_pm1(14, 0.4, 50 + seed),
+                  inputs.gaussian(10, 60 + seed)):
+            e_xy = O.xy_ground_state(J, n_starts=32, seed=seed)[0]
+            e_is = O.ground_state_bruteforce(J)[0]
+            assert e_xy <= e_is + 1e-12 * abs(e_is)
+        rng = np.random.default_rng(seed)
+        tau = rng.choice([-1.0, 1.0], size=11)
+        A = np.abs(inputs.gaussian(11, 70 + seed))
+        J = A * np.outer(tau, tau)
+        e_xy = O.xy_ground_state(J, n_starts=16, seed=seed)[0]
+        assert e_xy == pytest.approx(-np.sum(A), rel=1e-10)
+        assert O.ground_state_bruteforce(J)[0] == pytest.approx(-np.sum(A), rel=1e-12)
+
+
+def test_xy_ground_state_against_a_grid_of_angles():
+    """Brute force on tiny inputs: with theta_0 = 0 (a common rotation keeps E), a grid of
+    the other angles comes within the curvature bound of the minimiser's energy and never
+    below it.  E(grid) - E_min <= |H| (N-1) h^2 / 8 with |H| <= 4 max_p sum_q |J_pq|."""
+    n = 72
+    g = np.arange(n) * (2 * np.pi / n)
+    for seed in range(3):
+        J = inputs.gaussian(4, 80 + seed)
+        e_min, th = O.xy_ground_state(J, n_starts=32, seed=seed)
+        t1, t2, t3 = np.meshgrid(g, g, g, indexing="ij")
+        T = [np.zeros_like(t1), t1, t2, t3]
+        E = np.zeros_like(t1)
+        for p in range(4):
+            for q in range(4):
+                E -= J[p, q] * np.cos(T[p] - T[q])
+        e_grid = float(E.min())
+        bound = 4 * np.max(np.sum(np.abs(J), axis=1)) * 3 * (2 * np.pi / n) ** 2 / 8
+        assert e_min <= e_grid + 1e-12
+        assert e_grid - e_min <= bound
+        # the minimiser's angles: every spin is aligned with its local field
+        f = J @ np.stack([np.cos(th), np.sin(th)], axis=1)
+        cross = f[:, 0] * np.sin(th) - f[:, 1] * np.cos(th)
+        assert np.max(np.abs(cross)) < 1e-6

@@ -12,7 +12,7 @@ import oracle.oracle as O
 import oracle.round_trip as RT
 from paper_2308_02329_gb300 import chym, inputs
 from paper_2308_02329_gb300 import round_trip as M
-from tests.helpers import oracle_params, oracle_schedule
+from tests.helpers import oracle_params, oracle_schedule, rel_err
 
 CAV = M.Cavity(a=0.95, d=0.1, beta=1.3)
 
@@ -99,16 +99,20 @@ def _map_on_gpu(J, D, gains, replicas, trips, prec, sigma, seed=3):
     (20, 3, chym.PREC_FP64, 60, 1e-10),
     (37, 8, chym.PREC_FP64, 40, 1e-10),
     (45, 2, chym.PREC_FP32, 30, 1e-4),      # SIMT FP32 path
-    (100, 4, chym.PREC_BF16X2, 30, 1e-3),   # small-N tensor-core path
-    (61, 1, chym.PREC_BF16X2, 30, 1e-3),    # the CIM as a map (D = 1)
-    (150, 2, chym.PREC_BF16X2, 30, 1e-3),   # large-N tensor-core path
+    (100, 4, chym.PREC_BF16X2, 30, 1e-4),   # small-N tensor-core path
+    (61, 1, chym.PREC_BF16X2, 30, 1e-4),    # the CIM as a map (D = 1)
+    (150, 2, chym.PREC_BF16X2, 30, 1e-4),   # large-N tensor-core path
 ])
 def test_map_mode_matches_the_literal_map(N, D, prec, trips, tol):
     """Kernels in map mode (three gains around threshold, one batch) against the literal
-    map of Eq. 1 and Eq. 2.  FP64: 1e-10 relative.  FP32: 30 trips of FP32 rounding
-    (2^-24 each, a few operations deep) stay far below 1e-4.  BF16 hi+lo: x carries about 16
-    significant bits and dt = 1 leaves the per-trip rounding (~2^-16) undamped, so over
-    30 trips the relative error stays below 30 * 2^-16 = 4.6e-4; the test takes 1e-3."""
+    map of Eq. 1 and Eq. 2, relative per (run, component).  FP64: 1e-10.  FP32: 30 trips of
+    FP32 rounding (2^-24 each, a few operations deep) stay far below 1e-4.  BF16 hi+lo:
+    x = hi + lo + r with |r| <= 2^-18 |x| (two round-to-nearest BF16 steps), and J = +-1 is
+    exact, so a trip's coupling term eps J x is off by eps sum_q J_pq r_q: independent
+    roundings of about 2^-18 |x| over N terms, i.e. about eps sqrt(N) 2^-18 |x|
+    (eps N <= 3 at these gains, so about 1e-6 |x| at N = 100).  The map contracts around
+    its fixed points at these gains, so the errors of 30 trips add up to at most
+    30 times that, 3e-5; the test takes 1e-4, the mixed-precision bound."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -118,7 +122,7 @@ def test_map_mode_matches_the_literal_map(N, D, prec, trips, tol):
     for X, A, E in _map_on_gpu(J, D, gains, 5, trips, prec, sigma=1e-3):
         assert np.all(np.isfinite(X))
         scale = max(np.max(np.abs(A)), 1e-300)
-        assert np.max(np.abs(X - A)) / scale <= tol
+        assert rel_err(X, A) <= tol
         s = np.where(A[:, :, 0] >= 0, 1, -1).astype(np.int8)
         sure = np.all(np.abs(A[:, :, 0]) > 1e-2 * scale, axis=1)   # no sign within rounding
         Eo = O.ising_energies(J, s)

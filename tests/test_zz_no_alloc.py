@@ -38,7 +38,8 @@ def _energies(torch, N, D, n_h, reps, seed, steps, kind=chym.J_PM1, graph="sk"):
 
 
 def _same(a, b):
-    assert a["hits"].tolist() == b["hits"].tolist()
+    if "hits" in a:
+        assert a["hits"].tolist() == b["hits"].tolist()
     if "hist" in a or "hist" in b:
         assert a["hist"].tolist() == b["hist"].tolist()
     for k in ("P_max", "W_range", "W_scan", "dE_mean", "best_E"):
@@ -79,3 +80,20 @@ def test_stats_noalloc_rejects_sizes_beyond_its_array(torch_cuda):
     with pytest.raises(chym.ChymError) as e:
         chym.stats_noalloc(d_E.data_ptr(), 8192, 8, chym.J_PM1, 0.0, n_bins=70000)
     assert e.value.status == chym.EINVAL
+
+
+def test_stats_noalloc_without_a_hits_buffer_over_many_pumps(torch_cuda):
+    # no per-pump buffer from the caller and more pumps than one 64-count slice: the
+    # figures that need every per-pump count (P_max, W) must still match chym_stats
+    torch = torch_cuda
+    n_h, reps = 96, 4
+    J, c, d_E = _energies(torch, 16, 2, n_h, reps, 11, 1500)
+    E_gs = O.ground_state_bruteforce(J)[0]
+    ref = c.stats(E_gs, n_bins=32)
+    assert ref["n_hits"] > 0
+    for _ in range(2):
+        got = chym.stats_noalloc(d_E.data_ptr(), n_h * reps, n_h, chym.J_PM1, E_gs, n_bins=32,
+                                 with_hits=False)
+        assert "hits" not in got
+        _same(got, ref)
+    c.close()
