@@ -86,6 +86,9 @@ WORKLOADS = {
                        "(32 h x 64 replicas), 20000 steps dt=0.01: coupling over the nonzeros of J",
                        [("moebius", "moebius", 2048), ("moebius4k", "moebius", 4096)], (3,), 32, 64, 20000,
                        compare_plain=False),
+    "sk20_fp64": Workload("sk20_fp64", "SK+-1 N=20, D=3, 256 runs (8 h x 32 replicas), 3000 steps "
+                          "dt=0.01 (1500 + 1500 annealing), FP64 oracle-comparison mode",
+                          [("sk", "sk", 20)], (3,), 8, 32, 3000, compare_plain=False),
     "map": Workload("map", "SK+-1 N=100, D=3, the cavity round-trip map of Eq. 1-2 (a=0.95, d=0.1, "
                     "beta=100), 32 gain values K = K_th (1 + dK), dK in [0, 0.25], 512 replicas "
                     "each (16384 runs), 20000 round trips", [("sk", "sk", 100)], (3,), 32, 512, 20000,
@@ -188,23 +191,121 @@ def measured_peaks():
         return dict(PEAK_FALLBACK), "fallback"
 
 
-def alu_ops_per_element(D, nnz_row, coupling_on_alu):
+def alu_ops_per_element(D, nnz_row, coupling_on_alu, wide_mul_ops=2):
     """Algorithmic ALU lane-operations per element-step (one x_{p,mu} advanced once).
 
-    Noise: one Philox4x32-10 block (10 rounds x [2 wide multiplies + 2 three-input
-    xors + 2 key adds] = 60 ops) per four normals (per spin and 4 components for D >= 3,
-    per 4/D spins for D <= 2), Box-Muller 12 ops per pair
-    (2 int->float, 2 scalings, log, radius scaling, sqrt, angle, sin, cos, 2 products).
-    Drift + Euler-Maruyama update: 6.5 ops (norm share, x^2, cubic/loss FMA, product,
-    coupling FMA, noise add).  Coupling on the ALU adds nnz_row FMAs (dense J: N)."""
+    Noise: one Philox4x32-10 block per four normals (per spin and 4 components for D >= 3,
+    per 4/D spins for D <= 2): 10 rounds x [2 products of 32 x 32 -> 64 bits + 2 three-input
+    xors + 2 key adds].  A 64-bit product is two 32-bit results (high and low word), each an
+    integer multiply, which the SM issues on its FMA-heavy pipe at half the FP32 FMA rate:
+    it counts wide_mul_ops = 2 lane-operations (1 gives the unweighted count), so a block
+    is 80 (60).  Box-Muller 12 ops per pair (2 int->float, 2 scalings, log, radius scaling,
+    sqrt, angle, sin, cos, 2 products).  Drift + Euler-Maruyama update: 6.5 ops (norm
+    share, x^2, cubic/loss FMA, product, coupling FMA, noise add).  Coupling on the ALU
+    adds nnz_row FMAs (dense J: N)."""
     if D <= 2:      # the 4/D spins of a Philox block share it (all four normals used)
         blocks_per_el, pairs_per_el = 0.25, 0.5
     else:
         blocks_per_el, pairs_per_el = -(-D // 4) / D, -(-D // 2) / D
-    ops = 60.0 * blocks_per_el + 12.0 * pairs_per_el + 6.5
+    ops = 10.0 * (2 * wide_mul_ops + 4) * blocks_per_el + 12.0 * pairs_per_el + 6.5
     if coupling_on_alu:
         ops += nnz_row
     return ops
+
+
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal; no measured figure on this pool)
+
+
+def step_roofline(jobs, prec, steps_total, dur, clock_info, peaks, peak_src, prec_name):
+    """Roofline object of the step kernels of one timed region (dur: their span, s).
+
+    Large-N tensor-core contexts: algorithmic 2 N^2 D flops per run and step and the
+    issued products (K padded to 128, two BF16 products for +-1 J, three for real J)
+    against the sustained dense BF16 peak.  FP64 mode: the FP64 flops of the coupling
+    (2 N) and of the drift and update (10) per element against the nominal FP64 rate (the
+    noise's FP64 log and sine are not counted).  Otherwise the ALU lane-operations of
+    alu_ops_per_element against 152 SMs x 128 FP32 lanes at the median SM clock."""
+    from paper_2308_02329_gb300 import chym
+    large = any(j["N"] > 128 and not j["ctx"].uses_csr(prec) for j in jobs) and prec == chym.PREC_BF16X2
+    if large:
+        alg = steps_total * sum(2.0 * j["N"] ** 2 * j["D"] * j["runs"] for j in jobs)
+        issued = steps_total * sum(
+            2.0 * (128 * -(-j["N"] // 128)) ** 2 * j["D"] * j["runs"] *
+            (2 if j["name"] != "gauss" else 3) for j in jobs)
+        peak = peaks["bf16_tflops_sustained"] * 1e12
+        return {"bound": "tensor", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": alg / dur / peak, "traffic": None,
+                "issued_tflops": issued / dur / 1e12, "issued_frac": issued / dur / peak,
+                "kernel": "large-N tcgen05 step (BF16 hi+lo, FP32 accumulate)",
+                "peak_note": f"dense BF16 sustained, {peak_src}"}
+    if prec == chym.PREC_FP64:
+        alg = steps_total * sum((2.0 * j["N"] + 10.0) * j["N"] * j["D"] * j["runs"] for j in jobs)
+        peak = FP64_NOMINAL_TFLOPS * 1e12
+        return {"bound": "fp64", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": alg / dur / peak, "traffic": None,
+                "kernel": "SIMT step kernel (FP64)",
+                "peak_note": "nominal FP64 rate of the part (of nominal, not measured); "
+                             "coupling and update flops only, the noise transform uncounted"}
+    on_alu = prec == chym.PREC_FP32
+
+    def ops(wide):
+        return steps_total * sum(
+            alu_ops_per_element(j["D"], j["N"] if j["name"] in ("sk", "gauss") else j["nnz"],
+                                on_alu or j["ctx"].uses_csr(prec), wide) *
+            j["N"] * j["D"] * j["runs"] for j in jobs)
+    alg, alg1 = ops(2), ops(1)
+    sm_mhz = clock_info.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * sm_mhz * 1e6
+    return {"bound": "alu", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
+            "unit": "Tlane-op/s", "frac": alg / dur / peak, "traffic": None,
+            "frac_unweighted": alg1 / dur / peak,
+            "kernel": ("SIMT step kernel, coupling over the nonzeros of J (FP32)"
+                       if all(j["ctx"].uses_csr(prec) for j in jobs) else
+                       "SIMT step kernels (FP32)" if on_alu else "chym step kernel (" + prec_name + ")"),
+            "peak_note": "152 SMs x 128 FP32 lanes x median SM clock during the region; a 32-bit "
+                         "integer multiply counts 2 (half-rate pipe), frac_unweighted counts it 1"}
+
+
+REPLAY_RUNS, REPLAY_STEPS = 64, 400
+
+
+def replay_against_oracle(jobs, steps):
+    """64 runs of each context (every (runs/64)-th run, so every pump) replayed from their
+    seeds in a fresh context for `steps` steps on the GPU and on the FP64 oracle: the largest
+    state error relative to its own (run, component) scale, and the share of runs whose Ising
+    energies agree exactly."""
+    import oracle.oracle as O
+    from paper_2308_02329_gb300 import chym, inputs
+    out = {}
+    for j in jobs:
+        pick = np.linspace(0, j["runs"] - 1, REPLAY_RUNS).astype(int)
+        reps = j["runs"] // j["n_h"]
+        h_run = inputs.h_per_run(j["h"], reps)[pick]
+        seeds = np.ascontiguousarray(j["seeds"][pick])
+        J = j["J"]
+        ctx = chym.Context(J, j["D"], chym.J_REAL if j["name"] == "gauss" else chym.J_PM1)
+        sch = chym.Schedule(j["sched"].kind, j["sched"].k_anneal, j["sched"].k_total)
+        # one pump per replayed run: REPLAY_RUNS pump values, one replica each
+        ctx.run(j["prm"], h_run, seeds, steps, sch)
+        X, _ = ctx.get_state()
+        E = ctx.energy()
+        ctx.close()
+        t0 = time.perf_counter()
+        p = j["prm"]
+        Xo = O.run(J, j["D"], h_run, seeds,
+                   O.Params(dt=p.dt, sigma=p.sigma, init_std=p.init_std, gamma=p.gamma, kappa=p.kappa,
+                            eps=p.eps), O.Schedule(sch.kind, sch.k_anneal, sch.k_total), steps)
+        el = time.perf_counter() - t0
+        Eo = O.ising_energies(J, O.readout(Xo))
+        glob = float(np.max(np.abs(Xo)))
+        scale = np.maximum(np.max(np.abs(Xo), axis=1, keepdims=True), 1e-12 * glob)
+        err = np.max(np.abs(X - Xo) / scale, axis=(1, 2))
+        out[j["name"]] = {"runs": REPLAY_RUNS, "steps": steps, "of_steps": j["sched"].k_total,
+                          "state_rel_err_max": float(err.max()),
+                          "state_rel_err_median": float(np.median(err)),
+                          "energy_equal_frac": float(np.mean(E == Eo)),
+                          "oracle_seconds": el}
+    return out
 
 
 class ClockSampler:
@@ -501,7 +602,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chym", choices=["chym", "reference"])
     ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="bf16x2", choices=["bf16x2", "fp32"])
+    ap.add_argument("--prec", default="bf16x2", choices=["bf16x2", "fp32", "fp64"])
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -517,6 +618,8 @@ def main():
                     help="integration steps per run (default: the workload's); for profiling")
     ap.add_argument("--replicas", type=int, default=0,
                     help="replicas per pump value (default: the workload's); for profiling")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload: skip the one-step lines of the other configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -532,14 +635,56 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2308_02329_gb300 import chym, inputs
 
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = measure(args, w, sim_steps, rank, world, local)
+    if line is not None and world == 1 and args.workload == "n100" and not args.no_configs:
+        line["configs"] = {key: measure_config(args, key, rank, world, local) for key in EXTRA_CONFIGS}
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# One timed bench step of each of these, beside the default workload's line: the
+# FP64 oracle-comparison mode on its SK N=20 case and the two large-N workloads at
+# their full size (50000 steps each).
+EXTRA_CONFIGS = ("sk20_fp64", "sk1000", "sk800")
+
+
+def measure_config(args, key, rank, world, local):
+    """One timed step of workload `key` at its full size after three short warm-up steps
+    (WARM_STEPS integration steps each), with its own clocks, roofline, ground-state
+    hits and CPU baseline; for sk1000 also the replay of 64 runs against the oracle."""
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup = 1, 3
+    sub.prec = "fp64" if key == "sk20_fp64" else args.prec
+    sub.compare_plain, sub.no_e2e, sub.no_learned = False, True, True
+    w = WORKLOADS[key]
+    line = measure(sub, w, w.steps, rank, world, local, warm_steps=min(w.steps, WARM_STEPS),
+                   replay=key == "sk1000" and not args.no_cpu_baseline)
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "gs_hits_per_s",
+            "e_gs", "roofline", "cpu_baseline", "clocks", "gpu_launches", "replay64")
+    return {k: line[k] for k in keep if k in line}
+
+
+WARM_STEPS = 1000
+
+
+def measure(args, w, sim_steps, rank, world, local, warm_steps=None, replay=False):
+    """Set up a workload's contexts, warm up, time args.steps bench steps and return the
+    JSON line (rank 0; None on the other ranks).  warm_steps: integration steps of each
+    warm-up step (default: the full sim_steps)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2308_02329_gb300 import chym, inputs
+
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    prec = chym.PREC_BF16X2 if args.prec == "bf16x2" else chym.PREC_FP32
+    prec = {"bf16x2": chym.PREC_BF16X2, "fp32": chym.PREC_FP32, "fp64": chym.PREC_FP64}[args.prec]
 
     # ---------------- setup (untimed): instances, references, device inputs ----------
     jobs, gs = [], {}
@@ -554,7 +699,7 @@ def main():
                 gs[name] = chym.ground_state_mobius(N)
             elif w.key == "uneven":
                 gs[name] = float("inf")    # best energy of the warm-up runs (below)
-            elif kind == "sparse" and N <= 24:
+            elif N <= 24:
                 c1 = chym.Context(J, 1, jkind)
                 gs[name] = c1.ground_state_exact()[0]
                 c1.close()
@@ -571,6 +716,7 @@ def main():
         sd = INSTANCE_SEED + 7919 * rank + 97 * gi + D if seed is None else seed + D
         seeds = inputs.run_seeds(sd, runs)
         jobs.append(dict(name=name, N=N, D=D, ctx=ctx, kappa=sp["kappa"], skind=sp["skind"],
+                         J=J if replay else None,
                          gain_rel=sp.get("gain_rel"),
                          gamma=sp["gamma"], mode=sp.get("mode"), n_h=n_h, runs=runs, h=h,
                          seeds=seeds, d_h=torch.from_numpy(h).to(dev),
@@ -608,10 +754,11 @@ def main():
         tuning = batch.tune([j["prm"] for j in jobs], [j["sched"] for j in jobs],
                             probe_steps=min(256, sim_steps), stream=stream.cuda_stream)
 
-    def one_step(record=False):
+    def one_step(record=False, steps=None):
         """init every (graph, D), integrate all of them together as one batch (persistent
-        launches spread over all SMs), energies and the ground-state statistics.
-        Device inputs.  Returns the ground-state hits of this step."""
+        launches spread over all SMs) for `steps` (default: sim_steps) steps, energies
+        and the ground-state statistics.  Device inputs.  Returns the ground-state hits
+        of this step."""
         flush.fill_(1.0)
         sp = stream.cuda_stream
         for j in jobs:
@@ -620,7 +767,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=record)
         e1 = torch.cuda.Event(enable_timing=record)
         e0.record(stream)
-        batch.run([j["prm"] for j in jobs], [j["sched"] for j in jobs], sim_steps, sp)
+        batch.run([j["prm"] for j in jobs], [j["sched"] for j in jobs], steps or sim_steps, sp)
         e1.record(stream)
         for j in jobs:
             if "seg" not in j:
@@ -658,7 +805,7 @@ def main():
 
     # warm-up; the references of non-exact instances also take the best energy found
     for _ in range(args.warmup):
-        one_step()
+        one_step(steps=warm_steps)
     torch.cuda.synchronize()
     for j in jobs:
         if "seg" in j:
@@ -685,30 +832,8 @@ def main():
         ends = [fork.elapsed_time(e1) for _, e1 in marks]
         dur += (max(ends) - min(starts)) / 1e3
     peaks, peak_src = measured_peaks()
-    large = any(j["N"] > 128 and not j["ctx"].uses_csr(prec) for j in jobs) and prec == chym.PREC_BF16X2
-    if large:
-        alg = args.steps * sum(2.0 * j["N"] ** 2 * j["D"] * j["runs"] * sim_steps for j in jobs)
-        issued = args.steps * sum(
-            2.0 * (128 * -(-j["N"] // 128)) ** 2 * j["D"] * j["runs"] * sim_steps *
-            (2 if j["name"] != "gauss" else 3) for j in jobs)
-        peak = peaks["bf16_tflops_sustained"] * 1e12
-        roofline = {"bound": "tensor", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
-                    "unit": "TFLOP/s", "frac": alg / dur / peak, "traffic": None,
-                    "issued_tflops": issued / dur / 1e12,
-                    "kernel": "large-N tcgen05 step (BF16 hi+lo, FP32 accumulate)",
-                    "peak_note": f"dense BF16 sustained, {peak_src}"}
-    else:
-        on_alu = prec == chym.PREC_FP32
-        alg = args.steps * sum(
-            alu_ops_per_element(j["D"], j["N"] if j["name"] == "sk" else j["nnz"], on_alu or j["ctx"].uses_csr(prec)) *
-            j["N"] * j["D"] * j["runs"] * sim_steps for j in jobs)
-        sm_mhz = clock_info.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * sm_mhz * 1e6
-        roofline = {"bound": "alu", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
-                    "unit": "Tlane-op/s", "frac": alg / dur / peak, "traffic": None,
-                    "kernel": ("SIMT step kernel, coupling over the nonzeros of J (FP32)"
-                               if all(j["ctx"].uses_csr(prec) for j in jobs) else "chym step kernel (" + args.prec + ")"),
-                    "peak_note": "152 SMs x 128 FP32 lanes x median SM clock during the region"}
+    roofline = step_roofline(jobs, prec, args.steps * sim_steps, dur, clock_info, peaks, peak_src,
+                             args.prec)
 
     # ---------------- the plain FP32 form on the same workload ----------------
     plain = None
@@ -717,9 +842,15 @@ def main():
         one_step()
         el_p, hits_p = timed_region(args.steps)
         set_prec(prec)
+        dur_p = 0.0
+        for fork, marks in spans:
+            dur_p += (max(fork.elapsed_time(e1) for _, e1 in marks) -
+                      min(fork.elapsed_time(e0) for e0, _ in marks)) / 1e3
         plain = {"value": work_step * args.steps * world / el_p, "unit": UNIT,
                  "gs_hits_per_s": hits_p / el_p, "ms_per_step": 1e3 * el_p / args.steps,
-                 "dtype": "f32", "form": "SIMT FP32 coupling product, same workload"}
+                 "dtype": "f32", "form": "SIMT FP32 coupling product, same workload",
+                 "roofline": step_roofline(jobs, chym.PREC_FP32, args.steps * sim_steps, dur_p,
+                                           clock_info, peaks, peak_src, "fp32")}
 
     # ---------------- e2e: host inputs through the public API ----------------
     e2e = None
@@ -807,7 +938,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x2+f32" if prec == chym.PREC_BF16X2 else "f32",
+                "dtype": {chym.PREC_BF16X2: "bf16x2+f32", chym.PREC_FP32: "f32"}.get(prec, "f64"),
                 "data": "synthetic", "config": workload_config(w, args.prec, sim_steps),
                 "gs_hits_per_s": hits_total / elapsed,
                 "e_gs": {k: float(v) for k, v in gs.items()},
@@ -829,13 +960,14 @@ def main():
         if learned is not None:
             line["learned"] = learned
             line["gs_hits_ratio_learned_vs_plain"] = learned.get("ratio_vs_plain_fp32")
-        print(json.dumps(line), flush=True)
+        if replay:
+            line["replay64"] = replay_against_oracle(jobs, REPLAY_STEPS)
+    else:
+        line = None
     batch.close()
     for j in jobs:
         j["ctx"].close()
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+    return line
 
 
 if __name__ == "__main__":

@@ -244,6 +244,15 @@ chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J64, J, nn * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J32, j32.data(), nn * sizeof(float), cudaMemcpyHostToDevice);
+  {  // rows padded to 16 bytes for the vector loads of the tiled FP32 kernel
+    const int ld = (N + 3) / 4 * 4;
+    std::vector<float> jp((size_t)N * ld, 0.f);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) jp[(size_t)i * ld + j] = j32[(size_t)i * N + j];
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_J32p, jp.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_J32p, jp.data(), jp.size() * sizeof(float), cudaMemcpyHostToDevice);
+    c->j32p_ld = ld;
+  }
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J8, j8.data(), nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
   // sparse J: compressed rows for the CUDA-core product
@@ -294,6 +303,7 @@ chym_status chym_destroy(chym_ctx* c) {
   if (!c) return CHYM_OK;
   free_dev(c->d_J64);
   free_dev(c->d_J32);
+  free_dev(c->d_J32p);
   free_dev(c->d_J8);
   free_dev(c->d_Jbf16);
   free_dev(c->d_X);

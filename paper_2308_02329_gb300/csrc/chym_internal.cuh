@@ -169,6 +169,8 @@ struct chym_ctx {
   // device copies of J
   double* d_J64 = nullptr;    // FP64 N x N
   float* d_J32 = nullptr;     // FP32 N x N
+  float* d_J32p = nullptr;    // FP32 N x j32p_ld, rows zero padded to a multiple of 4
+  int j32p_ld = 0;
   int8_t* d_J8 = nullptr;     // int8 N x N (+-1/0 couplings only)
   // J in compressed rows when it is sparse (at most N^2 / 16 nonzeros): the coupling
   // product then runs on the CUDA cores over the nonzeros only

@@ -1,16 +1,18 @@
 // chym_simt.cu -- SIMT step kernels (FP64 oracle-comparison mode and the plain
 // FP32 form) and the initial-state kernel.
 //
-// One CTA owns RC runs for the whole launch and keeps their state in shared
-// memory across all steps; J (N x N) is staged in shared memory when it fits
-// and read through L1/L2 otherwise.  A sparse J (N > 128, at most N^2 / 16
-// nonzeros) is read as compressed rows instead, so the product costs 2 nnz D flops
-// per run and step rather than 2 N^2 D.  Per step:
-//   phase A  y_{p,mu} = sum_q J_pq x_{q,mu}  (C = J_N (x) 1_D, Eq. 1), J symmetric
-//            so thread p reads column p of row q (consecutive p: no bank conflict);
-//            each thread blocks RB runs so one J load feeds RB*D FMAs;
+// Every step kernel owns RC runs per CTA for the whole launch and keeps their state
+// in shared memory across all steps.  A sparse J (at most N^2 / 16 nonzeros) is read
+// as compressed rows, so the product costs 2 nnz D flops per run and step rather
+// than 2 N^2 D.  Per step:
+//   phase A  y_{p,mu} = sum_q J_pq x_{q,mu}  (C = J_N (x) 1_D, Eq. 1);
 //   phase B  x <- x + dt [(h-1) x - kappa x^3 - gamma x |x_p|^2 + eps alpha_mu y]
 //            + sigma sqrt(dt) xi  with xi from Philox4x32-10 + Box-Muller.
+// FP32 runs on the register-tiled kernel (step_simt_tiled_kernel, below), whose
+// threads each own 4 spins x RB runs through both phases; FP64, and FP32 where a
+// tile's state does not fit, run on the per-spin kernel (step_simt_kernel), whose
+// threads each take one (spin, run group) in phase A and one (spin, run) in phase B,
+// with J staged in shared memory when it fits and read through L1/L2 otherwise.
 #include <algorithm>
 
 #include "chym_internal.cuh"
@@ -74,6 +76,40 @@ __device__ __forceinline__ void spin_normals(uint64_t seed, uint32_t tag, uint64
       if (4 * blk + j < D) z[4 * blk + j] = zz[j];
   }
   }
+}
+
+// FP32 Box-Muller on the SFU approximations with denormals flushed (no argument or
+// result of the transform is denormal): u = (w + 1/2) 2^-32, r = scale sqrt(-2 ln u_r),
+// angle 2 pi u_a - pi, and the pair negated back (cos t = -cos(t - pi), likewise sin).
+__device__ __forceinline__ void box_muller_sfu(uint32_t wr, uint32_t wa, float scale, float& z0,
+                                               float& z1) {
+  const float ur = __fmaf_rn((float)wr, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float ua = __fmaf_rn((float)wa, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  float l2, r, s, c;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(ur));
+  const float r2 = l2 * (-1.3862943611198906f * scale * scale);  // -2 ln 2 scale^2 log2 u
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
+  const float t = __fmaf_rn(ua, 6.2831853071795865f, -3.1415926535897932f);
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(t));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(t));
+  z0 = -r * c;
+  z1 = -r * s;
+}
+
+// Philox4x32-10 with the ten round keys precomputed (two rounds per uint4).
+__device__ __forceinline__ uint4 philox_rounds(uint4 c, const uint4* rk) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const uint4 kk = rk[i];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t k0 = h ? kk.z : kk.x, k1 = h ? kk.w : kk.y;
+      const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
+      const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+      c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+  }
+  return c;
 }
 
 template <typename T, int D>
@@ -190,9 +226,257 @@ __global__ void __launch_bounds__(CSR && sizeof(T) == 4 ? 1024 : 512) step_simt_
   for (int i = tid; i < nr * N * D; i += nt) Xg[(size_t)run0 * N * D + i] = Xs[i];
 }
 
+// ---------------------------------------------------------------------------
+// Register-tiled FP32 form (the plain FP32 form: dense J, or the nonzeros of a sparse J).
+// The CTA keeps its RC runs in shared memory as Xs[q][r][DP] (spin-major, the runs of
+// one spin contiguous, components padded to DP).  Thread (tp, rg) owns the tile of
+// spins 4 tp .. 4 tp + 3 and runs RB rg .. RB rg + RB - 1.  Dense J: per q it loads the
+// four couplings J_{q, 4tp..4tp+3} (J symmetric, rows zero padded to NP; one 16-byte
+// read-only load that stays in L1) and the RB x DP state values of its runs (16-byte
+// shared loads) for 4 RB D FMAs.  Sparse J: per nonzero J_pq of each of its spins the
+// same RB x DP state values for RB D FMAs.  The thread then updates its own tile, so the
+// coupling product never leaves registers, and its noise follows the counter layout of
+// the other kernels; a tile of four spins holds whole Philox blocks for D <= 2.
+// (J in shared memory instead of L1 measured slower: it leaves fewer CTAs per SM.)
+template <int D, bool CSR>
+struct TileCfg {
+  static constexpr int DP = D == 3 ? 4 : (D > 4 ? 8 : D);
+  static constexpr int RB = D == 1 ? 8 : D <= 4 ? 4 : 2;
+  static_assert(RB * DP <= 2 || (RB * DP) % 4 == 0, "state loads are 4, 8 or 16k bytes");
+};
+
+// The n = RB DP consecutive state values of one spin and run group (n = 1, 2 or 4k).
+template <int n>
+__device__ __forceinline__ void load_x(const float* src, float (&xv)[n]) {
+  if constexpr (n == 1) {
+    xv[0] = src[0];
+  } else if constexpr (n == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(src);
+    xv[0] = t.x;
+    xv[1] = t.y;
+  } else {
+#pragma unroll
+    for (int v = 0; v < n / 4; ++v) {
+      const float4 t = reinterpret_cast<const float4*>(src)[v];
+      xv[4 * v] = t.x;
+      xv[4 * v + 1] = t.y;
+      xv[4 * v + 2] = t.z;
+      xv[4 * v + 3] = t.w;
+    }
+  }
+}
+
+template <int D, bool CSR>
+__global__ void __launch_bounds__(512) step_simt_tiled_kernel(const float* __restrict__ Jp,
+                                                              float* __restrict__ Xg,
+                                                              const double* __restrict__ hg,
+                                                              const uint64_t* __restrict__ seeds,
+                                                              StepConsts sc, int RC, int NP,
+                                                              CsrRows<float> csr) {
+  using Cfg = TileCfg<D, CSR>;
+  constexpr int DP = Cfg::DP, RB = Cfg::RB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = sc.N;
+  float* Xs = reinterpret_cast<float*>(smem_raw);                     // NP x RC x DP
+  uint4* s_rk = reinterpret_cast<uint4*>(Xs + (size_t)NP * RC * DP);  // RC x 5 round keys
+  int64_t* s_koff = reinterpret_cast<int64_t*>(s_rk + (size_t)RC * 5);
+  float* s_hm1 = reinterpret_cast<float*>(s_koff + RC);
+  const int run0 = blockIdx.x * RC;
+  const int nr = min(RC, sc.n_runs - run0);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tiles_p = NP / 4;
+  const int tp = tid % tiles_p, rg = tid / tiles_p;
+  const int p0 = 4 * tp, r0 = RB * rg;
+  const bool active = rg < RC / RB;
+
+  for (int i = tid; i < NP * RC * DP; i += nt) {
+    const int mu = i % DP, r = (i / DP) % RC, p = i / (DP * RC);
+    Xs[i] = (mu < D && p < N && r < nr) ? Xg[((size_t)(run0 + r) * N + p) * D + mu] : 0.f;
+  }
+  for (int r = tid; r < RC; r += nt) {
+    uint32_t k0 = 0u, k1 = 0u;
+    float hm1 = 0.f;
+    int64_t ko = 0;
+    if (r < nr) {
+      const int run = run0 + r;
+      k0 = (uint32_t)seeds[run];
+      k1 = (uint32_t)(seeds[run] >> 32);
+      hm1 = (float)(hg[sc.hidx[run]] - 1.0);
+      ko = sc.koff[run];
+    }
+    for (int i = 0; i < 5; ++i)  // Weyl key schedule: round j uses key + j (W0, W1)
+      s_rk[r * 5 + i] = make_uint4(k0 + (2u * i) * kPhiloxW0, k1 + (2u * i) * kPhiloxW1,
+                                   k0 + (2u * i + 1u) * kPhiloxW0, k1 + (2u * i + 1u) * kPhiloxW1);
+    s_koff[r] = ko;
+    s_hm1[r] = hm1;
+  }
+  __syncthreads();
+
+  const float dt = (float)sc.dt, gamma = (float)sc.gamma, kappa = (float)sc.kappa;
+  const float nscale = (float)sc.noise_scale;
+  const float inv_ramp = sc.sched_kind == 1 ? 1.f / (float)(sc.k_total - sc.k_anneal) : 0.f;
+  float edt[4];  // dt eps w_p of the tile's spins
+  int e_beg[4], e_end[4];  // the tile's compressed rows
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int p = p0 + i;
+    edt[i] = (float)(sc.dt * sc.eps) * ((sc.w && p < N) ? (float)sc.w[p] : 1.f);
+    e_beg[i] = e_end[i] = 0;
+    if (CSR && p < N) {
+      e_beg[i] = __ldg(csr.rp + p);
+      e_end[i] = __ldg(csr.rp + p + 1);
+    }
+  }
+  const float* xcol = Xs + (size_t)r0 * DP;
+  for (int64_t k = sc.k0; k < sc.k0 + sc.steps; ++k) {
+    float acc[4][RB][D];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) acc[i][b][mu] = 0.f;
+    // ---- coupling product y = (J (x) 1_D) x of the tile, in registers ----
+    if (active) {
+      if constexpr (CSR) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          for (int e = e_beg[i]; e < e_end[i]; ++e) {
+            const float j = __ldg(csr.cv + e);
+            float xv[RB * DP];
+            load_x<RB * DP>(xcol + (size_t)__ldg(csr.ci + e) * RC * DP, xv);
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+#pragma unroll
+              for (int mu = 0; mu < D; ++mu) acc[i][b][mu] = fmaf(j, xv[b * DP + mu], acc[i][b][mu]);
+          }
+        }
+      } else {
+#pragma unroll 2
+        for (int q = 0; q < N; ++q) {
+          const float4 jv = __ldg(reinterpret_cast<const float4*>(Jp + (size_t)q * NP + p0));
+          const float jq[4] = {jv.x, jv.y, jv.z, jv.w};
+          float xv[RB * DP];
+          load_x<RB * DP>(xcol + (size_t)q * RC * DP, xv);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+#pragma unroll
+              for (int mu = 0; mu < D; ++mu) acc[i][b][mu] = fmaf(jq[i], xv[b * DP + mu], acc[i][b][mu]);
+        }
+      }
+    }
+    __syncthreads();  // every read of the old state precedes the first update
+    // ---- drift, annealing scale and noise of the tile ----
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int r = r0 + b;
+        if (r >= nr) continue;
+        const int64_t kl = k - s_koff[r];
+        float ramp = 1.f;  // alpha_mu(kl) for mu >= 1
+        if (sc.sched_kind == 1 && kl >= sc.k_anneal)
+          ramp = kl >= sc.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(kl - sc.k_anneal) * inv_ramp);
+        const float a1 = 1.f + dt * s_hm1[r];
+        const uint4* rk = s_rk + r * 5;
+        float z[4][D];
+        if constexpr (D == 1) {
+          const uint4 w = philox_rounds(noise_counter((uint32_t)tp, 0u, 0u, (uint64_t)kl), rk);
+          box_muller_sfu(w.x, w.y, nscale, z[0][0], z[1][0]);
+          box_muller_sfu(w.z, w.w, nscale, z[2][0], z[3][0]);
+        } else if constexpr (D == 2) {
+#pragma unroll
+          for (int hb = 0; hb < 2; ++hb) {
+            const uint4 w = philox_rounds(noise_counter((uint32_t)(2 * tp + hb), 0u, 0u, (uint64_t)kl), rk);
+            box_muller_sfu(w.x, w.y, nscale, z[2 * hb][0], z[2 * hb][1]);
+            box_muller_sfu(w.z, w.w, nscale, z[2 * hb + 1][0], z[2 * hb + 1][1]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+              const uint4 w = philox_rounds(noise_counter((uint32_t)(p0 + i), (uint32_t)blk, 0u, (uint64_t)kl), rk);
+              float zz[4];
+              box_muller_sfu(w.x, w.y, nscale, zz[0], zz[1]);
+              if (D - 4 * blk > 2) box_muller_sfu(w.z, w.w, nscale, zz[2], zz[3]);
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (4 * blk + j < D) z[i][4 * blk + j] = zz[j];
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int p = p0 + i;
+          if (p >= N) continue;
+          float* x = Xs + ((size_t)p * RC + r) * DP;
+          float xv[D];
+          float n2 = 0.f;
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) {
+            xv[mu] = x[mu];
+            n2 = fmaf(xv[mu], xv[mu], n2);
+          }
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) {
+            const float xm = xv[mu];
+            // x + dt [(h-1) x - kappa x^3 - gamma x |x_p|^2 + eps w_p alpha_mu y] + noise
+            const float lin = a1 - dt * (kappa * xm * xm + gamma * n2);
+            const float ea = mu == 0 ? edt[i] : edt[i] * ramp;
+            x[mu] = fmaf(xm, lin, fmaf(ea, acc[i][b][mu], z[i][mu]));
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nr * N * D; i += nt) {
+    const int mu = i % D, p = (i / D) % N, r = i / (D * N);
+    Xg[(size_t)run0 * N * D + i] = Xs[((size_t)p * RC + r) * DP + mu];
+  }
+}
+
+// Launch of the tiled FP32 form; InvalidConfiguration when a run group does not fit its
+// shared memory (the caller then takes the per-spin kernel).
+template <int D, bool CSR>
+cudaError_t launch_simt_tiled(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
+  using Cfg = TileCfg<D, CSR>;
+  const int N = c->N, NP = c->j32p_ld;
+  const bool csr = CSR;
+  if (!csr && (!c->d_J32p || NP < N)) return cudaErrorInvalidConfiguration;
+  const size_t per_run = (size_t)NP * Cfg::DP * sizeof(float) + 5 * sizeof(uint4) + sizeof(int64_t) + sizeof(float);
+  if (Cfg::RB * per_run > kSimtSmemBudget) return cudaErrorInvalidConfiguration;
+  // sparse J with long rows of state (N of about 1000 and more): the per-spin kernel,
+  // whose 1024-thread CTAs measured faster there than CTAs of a few run groups
+  if (CSR && kSimtSmemBudget / per_run < (size_t)(4 * Cfg::RB)) return cudaErrorInvalidConfiguration;
+  int RC = (int)std::min<size_t>(kSimtSmemBudget / per_run, 512);
+  RC = RC / Cfg::RB * Cfg::RB;
+  // at most 512 threads, and no larger CTAs than it takes to fill the GPU
+  while (RC > Cfg::RB && (NP / 4) * (RC / Cfg::RB) > 512) RC -= Cfg::RB;
+  if ((NP / 4) * (RC / Cfg::RB) > 512) return cudaErrorInvalidConfiguration;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  while (RC > Cfg::RB && (int64_t)((sc.n_runs + RC - 1) / RC) < sms) RC -= Cfg::RB;
+  const int threads = std::max(32, ((NP / 4) * (RC / Cfg::RB) + 31) / 32 * 32);
+  const size_t smem = (size_t)RC * per_run;
+  const int grid = (sc.n_runs + RC - 1) / RC;
+  const CsrRows<float> rows{c->d_rp, c->d_ci, c->d_cv32};
+  auto kern = step_simt_tiled_kernel<D, CSR>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, threads, smem, st>>>(c->d_J32p, (float*)c->d_X, c->d_h, c->d_seeds, sc, RC, NP, rows);
+  return cudaGetLastError();
+}
+
 template <typename T, int D>
 cudaError_t launch_simt_typed(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
   const bool csr = c->sparse;  // the SIMT kernels use the compressed rows whenever they exist
+  if constexpr (sizeof(T) == 4) {
+    const cudaError_t e = csr ? launch_simt_tiled<D, true>(c, sc, st) : launch_simt_tiled<D, false>(c, sc, st);
+    if (e != cudaErrorInvalidConfiguration) return e;
+  }
   const int RB = csr ? 1 : SimtTraits<T>::RB;
   const int N = c->N;
   const size_t budget = kSimtSmemBudget;
