@@ -226,18 +226,33 @@ def step_roofline(jobs, prec, steps_total, dur, clock_info, peaks, peak_src, pre
     noise's FP64 log and sine are not counted).  Otherwise the ALU lane-operations of
     alu_ops_per_element against 152 SMs x 128 FP32 lanes at the median SM clock."""
     from paper_2308_02329_gb300 import chym
-    large = any(j["N"] > 128 and not j["ctx"].uses_csr(prec) for j in jobs) and prec == chym.PREC_BF16X2
+    tc = prec in (chym.PREC_BF16X2, chym.PREC_FP8)
+    large = any(j["N"] > 128 and not j["ctx"].uses_csr(prec) for j in jobs) and tc
     if large:
         alg = steps_total * sum(2.0 * j["N"] ** 2 * j["D"] * j["runs"] for j in jobs)
-        issued = steps_total * sum(
-            2.0 * (128 * -(-j["N"] // 128)) ** 2 * j["D"] * j["runs"] *
-            (2 if j["name"] != "gauss" else 3) for j in jobs)
+        # issued products: BF16 J x_hi, then J x_lo in BF16 (or in e4m3 at twice the rate in
+        # FP8 mode with +-1 J), plus J_lo x_hi for real J; in BF16-equivalent flops
+        bf16_eq, fp8 = 0.0, 0.0
+        for j in jobs:
+            f = 2.0 * (128 * -(-j["N"] // 128)) ** 2 * j["D"] * j["runs"] * steps_total
+            if j["name"] == "gauss":
+                bf16_eq += 3 * f
+            elif prec == chym.PREC_FP8:
+                bf16_eq += f + 0.5 * f
+                fp8 += f
+            else:
+                bf16_eq += 2 * f
         peak = peaks["bf16_tflops_sustained"] * 1e12
-        return {"bound": "tensor", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": alg / dur / peak, "traffic": None,
-                "issued_tflops": issued / dur / 1e12, "issued_frac": issued / dur / peak,
-                "kernel": "large-N tcgen05 step (BF16 hi+lo, FP32 accumulate)",
-                "peak_note": f"dense BF16 sustained, {peak_src}"}
+        out = {"bound": "tensor", "achieved": alg / dur / 1e12, "peak": peak / 1e12,
+               "unit": "TFLOP/s", "frac": alg / dur / peak, "traffic": None,
+               "issued_tflops": bf16_eq / dur / 1e12, "issued_frac": bf16_eq / dur / peak,
+               "kernel": "large-N tcgen05 step (BF16 hi + " +
+                         ("e4m3 lo for +-1 J" if prec == chym.PREC_FP8 else "BF16 lo") + ", FP32 accumulate)",
+               "peak_note": f"dense BF16 sustained, {peak_src}; FP8 products counted at half their flops "
+                            "(the e4m3 rate is twice the BF16 rate)"}
+        if fp8:
+            out["issued_fp8_tflops"] = fp8 / dur / 1e12
+        return out
     if prec == chym.PREC_FP64:
         alg = steps_total * sum((2.0 * j["N"] + 10.0) * j["N"] * j["D"] * j["runs"] for j in jobs)
         peak = FP64_NOMINAL_TFLOPS * 1e12
@@ -602,7 +617,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chym", choices=["chym", "reference"])
     ap.add_argument("--workload", default="n100", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="bf16x2", choices=["bf16x2", "fp32", "fp64"])
+    ap.add_argument("--prec", default="bf16x2", choices=["bf16x2", "fp8", "fp32", "fp64"])
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -652,7 +667,7 @@ def main():
 # One timed bench step of each of these, beside the default workload's line: the
 # FP64 oracle-comparison mode on its SK N=20 case and the two large-N workloads at
 # their full size (50000 steps each).
-EXTRA_CONFIGS = ("sk20_fp64", "sk1000", "sk800")
+EXTRA_CONFIGS = {"sk20_fp64": "fp64", "sk1000": "fp8", "sk800": "fp8"}
 
 
 def measure_config(args, key, rank, world, local):
@@ -661,7 +676,7 @@ def measure_config(args, key, rank, world, local):
     hits and CPU baseline; for sk1000 also the replay of 64 runs against the oracle."""
     sub = argparse.Namespace(**vars(args))
     sub.steps, sub.warmup = 1, 3
-    sub.prec = "fp64" if key == "sk20_fp64" else args.prec
+    sub.prec = EXTRA_CONFIGS[key]
     sub.compare_plain, sub.no_e2e, sub.no_learned = False, True, True
     w = WORKLOADS[key]
     line = measure(sub, w, w.steps, rank, world, local, warm_steps=min(w.steps, WARM_STEPS),
@@ -684,7 +699,8 @@ def measure(args, w, sim_steps, rank, world, local, warm_steps=None, replay=Fals
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    prec = {"bf16x2": chym.PREC_BF16X2, "fp32": chym.PREC_FP32, "fp64": chym.PREC_FP64}[args.prec]
+    prec = {"bf16x2": chym.PREC_BF16X2, "fp8": chym.PREC_FP8, "fp32": chym.PREC_FP32,
+            "fp64": chym.PREC_FP64}[args.prec]
 
     # ---------------- setup (untimed): instances, references, device inputs ----------
     jobs, gs = [], {}
@@ -750,7 +766,7 @@ def measure(args, w, sim_steps, rank, world, local, warm_steps=None, replay=Fals
         j["ctx"].run_device(j["prm"], j["d_h"].data_ptr(), j["n_h"], j["d_seeds"].data_ptr(),
                             j["runs"], 0, j["sched"], stream.cuda_stream)
     tuning = None
-    if prec == chym.PREC_BF16X2 and not args.no_tune:
+    if prec in (chym.PREC_BF16X2, chym.PREC_FP8) and not args.no_tune:
         tuning = batch.tune([j["prm"] for j in jobs], [j["sched"] for j in jobs],
                             probe_steps=min(256, sim_steps), stream=stream.cuda_stream)
 
@@ -927,7 +943,7 @@ def measure(args, w, sim_steps, rank, world, local, warm_steps=None, replay=Fals
         # context, one grouped GEMM launch per dimension and integration step, and one
         # step-counter kernel per 16-step graph; FP32/FP64 contexts and sparse ones take
         # one persistent SIMT launch each
-        bf16 = prec == chym.PREC_BF16X2
+        bf16 = prec in (chym.PREC_BF16X2, chym.PREC_FP8)
         small = [j for j in jobs if j["N"] <= 128 and bf16]
         large = [j for j in jobs if j["N"] > 128 and bf16 and not j["ctx"].uses_csr(prec)]
         sparse = [j for j in jobs if j["ctx"].uses_csr(prec)]
@@ -938,7 +954,8 @@ def measure(args, w, sim_steps, rank, world, local, warm_steps=None, replay=Fals
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {chym.PREC_BF16X2: "bf16x2+f32", chym.PREC_FP32: "f32"}.get(prec, "f64"),
+                "dtype": {chym.PREC_BF16X2: "bf16x2+f32", chym.PREC_FP8: "bf16+e4m3+f32",
+                          chym.PREC_FP32: "f32"}.get(prec, "f64"),
                 "data": "synthetic", "config": workload_config(w, args.prec, sim_steps),
                 "gs_hits_per_s": hits_total / elapsed,
                 "e_gs": {k: float(v) for k, v in gs.items()},

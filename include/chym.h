@@ -71,9 +71,17 @@ typedef enum {
 typedef enum {
   CHYM_PREC_FP64 = 0,   /* FP64 state and arithmetic (oracle-comparison mode) */
   CHYM_PREC_FP32 = 1,   /* FP32 state, FP32 SIMT coupling product (plain form) */
-  CHYM_PREC_BF16X2 = 2  /* FP32 state; J x on tcgen05 tensor cores with J in BF16 and
+  CHYM_PREC_BF16X2 = 2, /* FP32 state; J x on tcgen05 tensor cores with J in BF16 and
                            x split into BF16 hi + lo, FP32 accumulation (FP32 over
                            the nonzeros for very sparse large J, see chym_create) */
+  CHYM_PREC_FP8 = 3     /* as BF16X2, except that on the large-N path (N > 128) with
+                           +-1 couplings the lo half of x is held in FP8 e4m3 (both
+                           halves scaled by 2^16) and multiplied by J in e4m3 (exact
+                           for +-1) at twice the BF16 rate: x keeps about 13
+                           significant bits in the product (|x - hi - lo| <= 2^-13 |x|)
+                           instead of 17.  Elsewhere (N <= 128, real J) it runs as
+                           BF16X2.  The FP8 e4m3 coupling image of the +-1 J of the
+                           paper's SK instances is exact (text before Fig. 4). */
 } chym_prec;
 
 typedef struct {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libchym.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ESTATE = range(7)
 J_PM1, J_REAL = 0, 1
-PREC_FP64, PREC_FP32, PREC_BF16X2 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_BF16X2, PREC_FP8 = 0, 1, 2, 3
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP", 6: "ESTATE"}
 
 EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", "chym_run",
@@ -179,7 +179,7 @@ class Context:
 
     def uses_csr(self, prec):
         """Whether steps at precision prec run the coupling over the nonzeros of J."""
-        return self.sparse and (prec != PREC_BF16X2 or self.csr_bf16)
+        return self.sparse and (prec not in (PREC_BF16X2, PREC_FP8) or self.csr_bf16)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -48,7 +48,7 @@ chym_status check_params(const chym_params* prm) {
     return fail(CHYM_EINVAL, "init_std must be >= 0");
   if (!isfinite(prm->gamma) || !isfinite(prm->kappa) || !isfinite(prm->eps))
     return fail(CHYM_EINVAL, "gamma, kappa, eps must be finite");
-  if (prm->prec < CHYM_PREC_FP64 || prm->prec > CHYM_PREC_BF16X2)
+  if (prm->prec < CHYM_PREC_FP64 || prm->prec > CHYM_PREC_FP8)
     return fail(CHYM_EINVAL, "unknown precision");
   if (prm->flags != 0) return fail(CHYM_EINVAL, "params.flags must be 0");
   return CHYM_OK;
@@ -116,6 +116,7 @@ StepConsts make_step_consts(const chym_ctx* c, const chym_params* prm, const chy
   sc.koff = c->d_koff;
   sc.hidx = c->d_hidx;
   sc.w = c->d_w;
+  sc.fp8 = prm->prec == CHYM_PREC_FP8 ? 1 : 0;
   return sc;
 }
 
@@ -138,7 +139,7 @@ chym_status run_on_device(chym_ctx* c, const chym_params* prm, bool init, int64_
     c->prec = prm->prec;
   }
   c->have_energy = false;
-  if (steps > 0 && c->d_w && c->N > 128 && c->prec == CHYM_PREC_BF16X2 && !uses_csr(c, c->prec))
+  if (steps > 0 && c->d_w && c->N > 128 && is_tc_prec(c->prec) && !uses_csr(c, c->prec))
     return fail(CHYM_ENOTSUP, "coupling weights need N <= 128 on the tensor-core path");
   if (steps > 0) {
     const StepConsts sc = make_step_consts(c, prm, sched, c->k, steps);
@@ -189,7 +190,7 @@ cudaError_t launch_step(chym_ctx* c, const StepConsts& sc, int32_t prec, cudaStr
   // sparse J: the coupling over the nonzeros on the CUDA cores, FP32 state unless FP64
   if (uses_csr(c, prec)) return launch_step_simt(c, sc, prec == CHYM_PREC_FP64 ? prec : CHYM_PREC_FP32, st);
   if (prec == CHYM_PREC_FP64 || prec == CHYM_PREC_FP32) return launch_step_simt(c, sc, prec, st);
-  if (prec == CHYM_PREC_BF16X2)
+  if (is_tc_prec(prec))
     return c->N <= 128 ? launch_step_tc(c, sc, st) : launch_step_k2(c, sc, st);
   return cudaErrorNotSupported;
 }
@@ -559,7 +560,7 @@ chym_status chym_set_state(chym_ctx* c, const double* X, int n_runs, const doubl
   if (!c || !X || !h || !seeds) return fail(CHYM_EINVAL, "NULL argument");
   if (n_h < 1 || n_runs < 1 || n_runs % n_h) return fail(CHYM_EINVAL, "bad n_runs / n_h");
   if (k < 0) return fail(CHYM_EINVAL, "k must be >= 0");
-  if (prec < CHYM_PREC_FP64 || prec > CHYM_PREC_BF16X2) return fail(CHYM_EINVAL, "bad prec");
+  if (prec < CHYM_PREC_FP64 || prec > CHYM_PREC_FP8) return fail(CHYM_EINVAL, "bad prec");
   chym_status s = ensure_batch(c, n_runs, n_h);
   if (s != CHYM_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;

@@ -160,11 +160,11 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     const chym_schedule& s = schedules[i];
     if (c->prec < 0) return fail(CHYM_ESTATE, "every context needs a state (chym_run with seeds first)");
     if (!(p.dt > 0.0) || !(p.sigma >= 0.0) || p.flags != 0 || p.prec < CHYM_PREC_FP64 ||
-        p.prec > CHYM_PREC_BF16X2 || !isfinite(p.gamma) || !isfinite(p.kappa) || !isfinite(p.eps))
+        p.prec > CHYM_PREC_FP8 || !isfinite(p.gamma) || !isfinite(p.kappa) || !isfinite(p.eps))
       return fail(CHYM_EINVAL, "bad params in the batch");
     if ((c->prec == CHYM_PREC_FP64) != (p.prec == CHYM_PREC_FP64))
       return fail(CHYM_EINVAL, "a context cannot change between FP64 and FP32 storage");
-    if (c->d_w && c->N > 128 && p.prec == CHYM_PREC_BF16X2 && !uses_csr(c, p.prec))
+    if (c->d_w && c->N > 128 && is_tc_prec(p.prec) && !uses_csr(c, p.prec))
       return fail(CHYM_ENOTSUP, "coupling weights need N <= 128 on the tensor-core path");
     if ((s.kind != 0 && s.kind != 1) || s.reserved != 0 ||
         (s.kind == 1 && (s.k_anneal < 0 || s.k_total <= s.k_anneal)))
@@ -178,8 +178,8 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   std::vector<int> by_dim[9];
   for (int i = 0; i < n; ++i) {
     chym_ctx* c = b->ctxs[i];
-    if (params[i].prec == CHYM_PREC_BF16X2 && c->N <= 128) {
-      c->prec = CHYM_PREC_BF16X2;
+    if (is_tc_prec(params[i].prec) && c->N <= 128) {
+      c->prec = params[i].prec;
       by_dim[c->D].push_back(i);
       cudaError_t e = prepare_tc_operand(c);
       if (e != cudaSuccess) return cuda_fail(e, "J operand image");
@@ -200,7 +200,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   double small_total = total;
   for (int i = 0; i < n; ++i) {
     const chym_ctx* c = b->ctxs[i];
-    if (params[i].prec == CHYM_PREC_BF16X2 && c->N > 128 && !uses_csr(c, params[i].prec))
+    if (is_tc_prec(params[i].prec) && c->N > 128 && !uses_csr(c, params[i].prec))
       total += b->k2_cost * (double)k2_work_units(c->N, c->D, c->n_runs);
   }
   // SMs for the small-N dimensions (all of them when there is no large-N work)
@@ -295,9 +295,9 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     cudaStream_t s = b->streams[sidx];
     for (int i = 0; i < n; ++i) {
       chym_ctx* c = b->ctxs[i];
-      if (desc_of[i] >= 0 || params[i].prec != CHYM_PREC_BF16X2 || uses_csr(c, params[i].prec)) continue;
+      if (desc_of[i] >= 0 || !is_tc_prec(params[i].prec) || uses_csr(c, params[i].prec)) continue;
       if (idx.empty()) CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
-      c->prec = CHYM_PREC_BF16X2;
+      c->prec = params[i].prec;
       descs.resize(descs.size() + kb);
       const StepConsts sc = make_step_consts(c, &params[i], &schedules[i], c->k, steps);
       cudaError_t e = k2_prepare(c, sc, s, descs.data() + descs.size() - kb);

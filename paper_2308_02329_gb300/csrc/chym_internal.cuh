@@ -42,6 +42,7 @@ struct StepConsts {
   const int64_t* koff;        // per run: global step at which the run was (re)seeded
   const int32_t* hidx;        // per run: index of its pump value in h
   const double* w;            // per spin: weight of its coupling term (nullable: all 1)
+  int fp8;                    // CHYM_PREC_FP8: e4m3 lo operands on the large-N path
 };
 
 // Contiguous spin ranges [begin[i], begin[i + 1]) whose Ising energies are read
@@ -217,8 +218,11 @@ namespace chym {
 // slower and a run's state fits the SIMT kernel's shared memory: N >= 1024, D >= 3,
 // on average at most N / 256 nonzeros per row (nnz <= N^2 / 256) and
 // 2 N D sizeof(float) <= kSimtSmemBudget.
+// Precisions whose coupling product runs on the tensor cores (FP32 state, BF16 hi
+// part; FP8 mode differs from BF16X2 only in the lo operands of the large-N path).
+inline bool is_tc_prec(int32_t prec) { return prec == CHYM_PREC_BF16X2 || prec == CHYM_PREC_FP8; }
 inline bool uses_csr(const chym_ctx* c, int32_t prec) {
-  return c->sparse && (prec != CHYM_PREC_BF16X2 || c->csr_bf16);
+  return c->sparse && (!is_tc_prec(prec) || c->csr_bf16);
 }
 // kernel launchers (implemented in the .cu files)
 cudaError_t launch_init(chym_ctx* c, int32_t prec, cudaStream_t st, double init_std);

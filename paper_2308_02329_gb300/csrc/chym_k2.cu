@@ -15,7 +15,17 @@
 //              a core matrix (one coalesced store per component);
 //   Aimg[t][mt][kc]  J (t = 0) and, for real couplings, its BF16 residual
 //              (t = 1) as A-operand blocks of 128 rows x 32 K, K-major: core
-//              (row/8, k/8) at (row/8) * 512 + (k/8) * 128.
+//              (row/8, k/8) at (row/8) * 512 + (k/8) * 128; for +-1 couplings
+//              t = 1 holds J in FP8 e4m3 (exact), 4 KB blocks with core
+//              (row/8, k/16) at (row/8) * 256 + (k/16) * 128.
+// FP8 mode (+-1 couplings, CHYM_PREC_FP8): the lo half of the split is stored in
+// e4m3 instead of BF16, its blocks MN-major with core (col/16, k/8) at
+// (col/16) * 512 + (k/8) * 128 (16 columns of one byte per core row), and multiplied
+// by the e4m3 image of J with one kind::f8f6f4 product (K = 32) per K chunk at twice
+// the BF16 rate.  Both halves carry the scale S = 2^kLoScaleLog2 (exact in BF16), so
+// that x_lo S sits in the normal range of e4m3 (|x_lo| <= 2^-9 |x|); the hi and lo
+// products add into one FP32 accumulator holding S y, and the epilogue folds 1/S
+// into dt eps.  x_lo then keeps 4 significant bits: x = hi + lo within 2^-13 |x|.
 // One launch covers a table of tiles (context, M tile mt, column tile ct) that may
 // span many contexts of the same D, ordered with mt fastest so that the CTAs that
 // run at the same time share their column tile's B blocks in L2.  The grid is
@@ -37,6 +47,7 @@
 // on a timeout the CTA raises the status word, drains its own tensor-core and
 // copy work with bounded waits, frees TMEM and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <vector>
@@ -59,6 +70,8 @@ constexpr int kAccCols = 256;                  // TMEM columns of one accumulato
 constexpr size_t kRingBudget = 196 * 1024;     // shared memory for the stage ring
 constexpr int kTimeoutNs = 2000000000;
 constexpr int kGraphSteps = 16;                // steps per captured graph
+constexpr uint32_t kA8Block = 128 * kKc;       // bytes of an e4m3 A block (4 KB)
+constexpr int kLoScaleLog2 = 16;               // FP8 mode: B operands carry 2^16
 
 // Runs per column tile: a multiple of 32 (whole 4-run blocks for each of the four
 // warps of a TMEM lane quarter, and n = D * RT a multiple of 16), n <= 256.
@@ -76,6 +89,7 @@ struct K2Desc {
   const int64_t* koff;     // per run: global step of its (re)seeding
   unsigned long long buf_bytes;
   int N, KP, MT, KC, CT, RT, n, n_runs, a_terms, sched_kind;
+  int lo8;                 // 1: lo half in e4m3 (FP8 mode, +-1 couplings)
   int64_t k0, k_anneal, k_total;  // k0: step of the context when the call began
   float gdt, kdt, edt, neg2ln2s2, inv_ramp;
 };
@@ -106,6 +120,13 @@ struct K2Launch {
 };
 
 __host__ __device__ inline uint32_t b_block_bytes(int n) { return (uint32_t)n * kKc * 2u; }
+// bytes of a lo block: BF16, or e4m3 in FP8 mode
+__host__ __device__ inline uint32_t b_lo_bytes(int n, int lo8) { return (uint32_t)n * kKc * (lo8 ? 1u : 2u); }
+// bytes of one stage of a context: A (and its second term: the BF16 residual of real
+// J or the e4m3 J of FP8 mode), B hi and B lo
+__host__ __device__ inline uint32_t stage_bytes(int n, int a_terms, int lo8) {
+  return kABlock + (a_terms > 1 ? kABlock : lo8 ? kA8Block : 0u) + b_block_bytes(n) + b_lo_bytes(n, lo8);
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -150,6 +171,16 @@ __device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, uint32_t a_lo, uint3
       "setp.ne.b32 p, %5, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}\n" ::"r"(d_tmem),
       "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc), "r"(accumulate));
+}
+// D += A B on the tensor core, kind::f8f6f4 (e4m3 operands, K = 32, FP32 accumulator),
+// with the descriptors' low words and their own high words.
+__device__ __forceinline__ void mma_f8_w(uint32_t d_tmem, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
+                                         uint32_t b_hi, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .b64 da, db;\n\t"
+      "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %5, 1;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -262,6 +293,24 @@ __device__ __forceinline__ void store_hilo(uint8_t* hi_dst, uint8_t* lo_dst, con
   *reinterpret_cast<uint2*>(lo_dst) = make_uint2(lw[0], lw[1]);
 }
 
+// FP8 mode: 4 new values of one component as S bf16(v) (8 bytes, hi block) and
+// e4m3(S (v - bf16(v))) (4 bytes, lo block), S = 2^kLoScaleLog2.
+__device__ __forceinline__ void store_hilo8(uint8_t* hi_dst, uint8_t* lo_dst, const float (&v)[kRB]) {
+  constexpr float S = (float)(1u << kLoScaleLog2);
+  uint32_t hw[2], lw[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 hs = __floats2bfloat162_rn(hf.x * S, hf.y * S);  // exact
+    hw[j] = *reinterpret_cast<const uint32_t*>(&hs);
+    lw[j] = (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2((v[2 * j] - hf.x) * S, (v[2 * j + 1] - hf.y) * S),
+                                               __NV_SATFINITE, __NV_E4M3);
+  }
+  *reinterpret_cast<uint2*>(hi_dst) = make_uint2(hw[0], hw[1]);
+  *reinterpret_cast<uint32_t*>(lo_dst) = lw[0] | (lw[1] << 16);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -307,15 +356,18 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
         const K2Tile tile = L.tiles[t];
         const K2Desc& d = L.descs[tile.desc];
         // the tile's constants in registers (the loop's asm statements clobber memory)
-        const int KC = d.KC, terms = d.a_terms;
-        const uint32_t BB = b_block_bytes(d.n);
-        const uint32_t bytes = (uint32_t)terms * kABlock + 2u * BB;
+        const int KC = d.KC, terms = d.a_terms, lo8 = d.lo8;
+        const uint32_t BB = b_block_bytes(d.n), BL = b_lo_bytes(d.n, lo8);
+        const uint32_t bytes = stage_bytes(d.n, terms, lo8);
+        const uint32_t a2 = terms > 1 ? kABlock : lo8 ? kA8Block : 0u;  // second A term
         const uint8_t* a_src = d.Aimg + (size_t)tile.mt * KC * kABlock;       // term 0, K chunk 0
-        const size_t a_term = (size_t)d.MT * KC * kABlock;                    // to the residual term
-        const uint8_t* b_src = d.Xt + (size_t)(step & 1) * d.buf_bytes + (size_t)tile.ct * KC * BB;
-        const size_t lo_off = (size_t)d.CT * KC * BB;
+        const size_t a_term = (size_t)d.MT * KC * kABlock;                    // to the second term
+        const uint8_t* a2_src = d.Aimg + a_term + (size_t)tile.mt * KC * a2;
+        const uint8_t* bx = d.Xt + (size_t)(step & 1) * d.buf_bytes;
+        const uint8_t* b_src = bx + (size_t)tile.ct * KC * BB;
+        const uint8_t* bl_src = bx + (size_t)d.CT * KC * BB + (size_t)tile.ct * KC * BL;
         bool stop = false;
-        for (int kc = 0; kc < KC; ++kc, ++g, a_src += kABlock, b_src += BB) {
+        for (int kc = 0; kc < KC; ++kc, ++g, a_src += kABlock, a2_src += a2, b_src += BB, bl_src += BL) {
           const uint32_t s = g % (uint32_t)S;
           if (g >= (uint32_t)S && !mbar_wait(smem_addr(&empty_bar[s]), ((g / S) - 1u) & 1u)) {
             atomicOr(L.status, STATUS_TIMEOUT);
@@ -328,10 +380,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes)
                        : "memory");
           bulk_g2s(base, a_src, kABlock, fb);
-          if (terms > 1) bulk_g2s(base + kABlock, a_src + a_term, kABlock, fb);
-          const uint32_t bb = base + (uint32_t)terms * kABlock;
+          if (a2) bulk_g2s(base + kABlock, a2_src, a2, fb);
+          const uint32_t bb = base + kABlock + a2;
           bulk_g2s(bb, b_src, BB, fb);
-          bulk_g2s(bb + BB, b_src + lo_off, BB, fb);
+          bulk_g2s(bb + BB, bl_src, BL, fb);
         }
         if (stop) break;
       }
@@ -364,9 +416,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
         // costs one add; the high word (SBO, version) is the same for all of them.
         const uint32_t d_hi = (uint32_t)(smem_desc(0u, kCoreK, kCoreMN) >> 32);
         const uint32_t d_lo0 = (uint32_t)smem_desc(smem_addr(smem), kCoreK, kCoreMN);
-        const uint32_t o_bhi = ((uint32_t)d.a_terms * kABlock) >> 4, o_blo = o_bhi + (BB >> 4);
+        const bool real_j = d.a_terms > 1, lo8 = d.lo8 != 0;
+        const uint32_t a2 = real_j ? kABlock : lo8 ? kA8Block : 0u;
+        const uint32_t o_bhi = (kABlock + a2) >> 4, o_blo = o_bhi + (BB >> 4);
         const uint32_t o_alo = kABlock >> 4, stride16 = L.stage_stride >> 4;
-        const bool real_j = d.a_terms > 1;
+        // FP8 mode: e4m3 J (K-major, 8 x 16-byte cores, 256 bytes between row groups) and
+        // e4m3 lo (MN-major, 16 columns a core row, 512 bytes between column groups)
+        const uint32_t a8_hi = (uint32_t)(smem_desc(0u, kCoreK, 256u) >> 32);
+        const uint32_t idesc8 = (1u << 4) | (1u << 16) | ((uint32_t)(d.n >> 3) << 17) |
+                                ((uint32_t)(128 >> 4) << 24);
         const int KC = d.KC;
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const uint32_t s = g % (uint32_t)S;
@@ -376,12 +434,21 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = d_lo0 + s * stride16;
+          if (lo8) {
 #pragma unroll
-          for (int ks = 0; ks < kKc / 16; ++ks) {
-            const uint32_t a = a0 + (uint32_t)ks * (2u * kCoreK >> 4);
-            mma_bf16_w(acc, a, a + o_bhi, d_hi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-            mma_bf16_w(acc, a, a + o_blo, d_hi, idesc, 1u);
-            if (real_j) mma_bf16_w(acc, a + o_alo, a + o_bhi, d_hi, idesc, 1u);
+            for (int ks = 0; ks < kKc / 16; ++ks) {
+              const uint32_t a = a0 + (uint32_t)ks * (2u * kCoreK >> 4);
+              mma_bf16_w(acc, a, a + o_bhi, d_hi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+            }
+            mma_f8_w(acc, a0 + o_alo, a8_hi, a0 + o_blo, d_hi, idesc8);
+          } else {
+#pragma unroll
+            for (int ks = 0; ks < kKc / 16; ++ks) {
+              const uint32_t a = a0 + (uint32_t)ks * (2u * kCoreK >> 4);
+              mma_bf16_w(acc, a, a + o_bhi, d_hi, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+              mma_bf16_w(acc, a, a + o_blo, d_hi, idesc, 1u);
+              if (real_j) mma_bf16_w(acc, a + o_alo, a + o_bhi, d_hi, idesc, 1u);
+            }
           }
           mma_commit(smem_addr(&empty_bar[s]));
         }
@@ -413,11 +480,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
       const int p = tile.mt * 128 + q * 32 + lane;
       const bool live = p < dref.N;
       const uint32_t BB = b_block_bytes(dref.n);
+      const bool lo8 = dref.lo8 != 0;
+      const uint32_t BL = b_lo_bytes(dref.n, dref.lo8);
       uint8_t* Xt_next = dref.Xt + (size_t)((step + 1) & 1) * dref.buf_bytes;
-      const size_t lo_off = (size_t)dref.CT * dref.KC * BB;
-      // byte offset of this thread's spin (row k = p of the next step's B) in its block
-      const size_t row_off = ((size_t)tile.ct * dref.KC + (p / kKc)) * BB +
-                             (size_t)((p % kKc) >> 3) * kCoreK + (size_t)(p & 7) * 16u;
+      uint8_t* Xl_next = Xt_next + (size_t)dref.CT * dref.KC * BB;
+      // byte offset of this thread's spin (row k = p of the next step's B) in its hi and
+      // lo blocks
+      const size_t row_in = (size_t)((p % kKc) >> 3) * kCoreK + (size_t)(p & 7) * 16u;
+      const size_t row_off = ((size_t)tile.ct * dref.KC + (p / kKc)) * BB + row_in;
+      const size_t row_lo = ((size_t)tile.ct * dref.KC + (p / kKc)) * BL + row_in;
       const int run_tile = tile.ct * RT;
       float xc[D][kRB];
       load_block_x<D>(Xm, KP, n_runs, run_tile + kRB * e, p, live, xc);  // in flight during the products
@@ -518,7 +589,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
               const int mu = 4 * blk + m;
               const int col = mu * RT + kRB * rb;
               const size_t off = row_off + (size_t)(col >> 3) * kCoreMN + (size_t)(col & 7) * 2u;
-              store_hilo(Xt_next + off, Xt_next + lo_off + off, xc[mu]);
+              if (lo8)
+                store_hilo8(Xt_next + off, Xl_next + row_lo + (size_t)(col >> 4) * kCoreMN + (size_t)(col & 15),
+                            xc[mu]);
+              else
+                store_hilo(Xt_next + off, Xl_next + off, xc[mu]);  // BF16 lo blocks mirror hi
             }
           }
         }
@@ -550,9 +625,9 @@ __global__ void k2_advance_kernel(int64_t* done, int64_t by) { *done += by; }
 // buffer is zeroed beforehand, so padding spins and runs stay zero).
 __global__ void k2_pack_kernel(const float* __restrict__ X, float* __restrict__ Xm,
                                uint8_t* __restrict__ Xt, int N, int D, int KP, int KC, int CT,
-                               int RT, int n_runs) {
+                               int RT, int n_runs, int lo8) {
   const int n = D * RT;
-  const size_t BB = b_block_bytes(n);
+  const size_t BB = b_block_bytes(n), BL = b_lo_bytes(n, lo8);
   const size_t lo_off = (size_t)CT * KC * BB;
   const size_t total = (size_t)n_runs * D * KP;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
@@ -563,12 +638,19 @@ __global__ void k2_pack_kernel(const float* __restrict__ X, float* __restrict__ 
     const float v = p < N ? X[((size_t)run * N + p) * D + mu] : 0.f;
     Xm[c * KP + p] = v;
     const int ct = run / RT, cl = mu * RT + run % RT;
-    const size_t off = ((size_t)ct * KC + p / kKc) * BB + (size_t)(cl >> 3) * kCoreMN +
-                       (size_t)((p % kKc) >> 3) * kCoreK + (size_t)(p & 7) * 16 + (size_t)(cl & 7) * 2;
+    const size_t row_in = (size_t)((p % kKc) >> 3) * kCoreK + (size_t)(p & 7) * 16;
+    const size_t off = ((size_t)ct * KC + p / kKc) * BB + (size_t)(cl >> 3) * kCoreMN + row_in + (size_t)(cl & 7) * 2;
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    *reinterpret_cast<__nv_bfloat16*>(Xt + off) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(Xt + lo_off + off) = lo;
+    const float hf = __bfloat162float(hi);
+    if (lo8) {  // both halves scaled by 2^kLoScaleLog2, lo in e4m3 (see store_hilo8)
+      constexpr float S = (float)(1u << kLoScaleLog2);
+      *reinterpret_cast<__nv_bfloat16*>(Xt + off) = __float2bfloat16_rn(hf * S);
+      const size_t off8 = ((size_t)ct * KC + p / kKc) * BL + (size_t)(cl >> 4) * kCoreMN + row_in + (size_t)(cl & 15);
+      Xt[lo_off + off8] = (uint8_t)__nv_cvt_float_to_fp8((v - hf) * S, __NV_SATFINITE, __NV_E4M3);
+    } else {
+      *reinterpret_cast<__nv_bfloat16*>(Xt + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(Xt + lo_off + off) = __float2bfloat16_rn(v - hf);
+    }
   }
 }
 
@@ -607,7 +689,14 @@ __global__ void k2_aimg_kernel(const double* __restrict__ J, int N, int MT, int 
     const size_t off = ((size_t)mt * KC + kc) * (128 * kKc) + (size_t)(r / 8) * (kCoreMN / 2) +
                        (size_t)(kk / 8) * (kCoreK / 2) + (r % 8) * 8 + (kk % 8);  // in elements
     img[off] = hi;
-    if (terms > 1) img[per_term + off] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+    if (terms > 1) {
+      img[per_term + off] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+    } else {  // +-1 couplings: J in e4m3 (exact) after the BF16 blocks, K-major 8 x 16-byte cores
+      uint8_t* img8 = reinterpret_cast<uint8_t*>(img + per_term);
+      const size_t off8 = ((size_t)mt * KC + kc) * kA8Block + (size_t)(r / 8) * 256 + (size_t)(kk / 16) * 128 +
+                          (r % 8) * 16 + (kk % 16);
+      img8[off8] = (uint8_t)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
+    }
   }
 }
 
@@ -657,7 +746,8 @@ cudaError_t prepare_k2_operand(chym_ctx* c) {
   if (c->d_Ak2) return cudaSuccess;
   const int N = c->N, MT = (N + 127) / 128, KP = MT * 128, KC = KP / kKc;
   const int terms = c->kind == CHYM_J_PM1 ? 1 : 2;
-  const size_t bytes = (size_t)terms * MT * KC * kABlock;
+  // real J: J and its BF16 residual; +-1 J: J in BF16 and in e4m3 (FP8 mode)
+  const size_t bytes = (size_t)MT * KC * (kABlock + (terms > 1 ? kABlock : kA8Block));
   cudaError_t e = cudaMalloc(&c->d_Ak2, bytes);
   if (e != cudaSuccess) return e;
   k2_aimg_kernel<<<152 * 8, 256>>>(c->d_J64, N, MT, KC, terms, (__nv_bfloat16*)c->d_Ak2);
@@ -677,9 +767,11 @@ cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void*
   const int N = c->N, D = c->D, MT = (N + 127) / 128, KP = MT * 128, KC = KP / kKc;
   const int RT = k2_rt(D, sc.n_runs), n = D * RT;
   const int CT = (sc.n_runs + RT - 1) / RT;
-  const size_t BB = b_block_bytes(n);
+  const int lo8 = sc.fp8 && c->kind == CHYM_J_PM1 ? 1 : 0;
+  const size_t BB = b_block_bytes(n), BL = b_lo_bytes(n, lo8);
   const size_t xm_bytes = ((size_t)sc.n_runs * D * KP * 4 + 255) / 256 * 256;
-  const size_t xt_bytes = (size_t)2 * 2 * CT * KC * BB;
+  const size_t buf_bytes = ((size_t)CT * KC * (BB + BL) + 255) / 256 * 256;
+  const size_t xt_bytes = 2 * buf_bytes;
   const size_t ar_bytes = ((size_t)sc.n_runs * 4 + 255) / 256 * 256;
   const size_t need = xm_bytes + xt_bytes + ar_bytes;
   if (need > c->k2_ws_bytes) {
@@ -698,14 +790,14 @@ cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void*
   if (e != cudaSuccess) return e;
   k2_runconst_kernel<<<(sc.n_runs + 255) / 256, 256, 0, st>>>(c->d_h, c->d_hidx, sc.n_runs, sc.dt, ar);
   k2_pack_kernel<<<152 * 8, 256, 0, st>>>((const float*)c->d_X, Xm, Xt, N, D, KP, KC, CT, RT,
-                                           sc.n_runs);
+                                           sc.n_runs, lo8);
   d.Aimg = (const uint8_t*)c->d_Ak2;
   d.Xm = Xm;
   d.Xt = Xt;
   d.ar = ar;
   d.seeds = c->d_seeds;
   d.koff = c->d_koff;
-  d.buf_bytes = (unsigned long long)(2 * CT * KC * BB);
+  d.buf_bytes = (unsigned long long)buf_bytes;
   d.N = N;
   d.KP = KP;
   d.MT = MT;
@@ -715,13 +807,15 @@ cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void*
   d.n = n;
   d.n_runs = sc.n_runs;
   d.a_terms = c->kind == CHYM_J_PM1 ? 1 : 2;
+  d.lo8 = lo8;
   d.sched_kind = sc.sched_kind;
   d.k0 = sc.k0;
   d.k_anneal = sc.k_anneal;
   d.k_total = sc.k_total;
   d.gdt = (float)(sc.dt * sc.gamma);
   d.kdt = (float)(sc.dt * sc.kappa);
-  d.edt = (float)(sc.dt * sc.eps);
+  // FP8 mode: the accumulator holds 2^kLoScaleLog2 y (both operand halves carry it)
+  d.edt = (float)(sc.dt * sc.eps / (lo8 ? (double)(1u << kLoScaleLog2) : 1.0));
   d.neg2ln2s2 = (float)(-2.0 * 0.69314718055994531 * sc.noise_scale * sc.noise_scale);
   d.inv_ramp = sc.sched_kind == 1 ? (float)(1.0 / (double)(sc.k_total - sc.k_anneal)) : 0.f;
   return cudaGetLastError();
@@ -765,12 +859,12 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
       if (dims[i] == D) order.push_back(i);
     auto cost = [&](int i) {
       const K2Desc& d = *reinterpret_cast<const K2Desc*>(descs.data() + i * db);
-      return (long long)d.KP * d.n * d.a_terms;
+      return (long long)d.KP * d.n * (d.a_terms > 1 ? 6 : d.lo8 ? 3 : 4);  // in half BF16 products
     };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
     for (int i : order) {
       const K2Desc& d = *reinterpret_cast<const K2Desc*>(descs.data() + i * db);
-      const uint32_t bytes = (uint32_t)d.a_terms * kABlock + 2u * b_block_bytes(d.n);
+      const uint32_t bytes = stage_bytes(d.n, d.a_terms, d.lo8);
       dim_stride[D] = std::max(dim_stride[D], (bytes + 1023u) / 1024u * 1024u);
       for (int ct = 0; ct < d.CT; ++ct)
         for (int mt = 0; mt < d.MT; ++mt) tiles.push_back(K2Tile{i, mt, ct, 0});  // mt fastest

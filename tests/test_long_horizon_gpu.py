@@ -69,23 +69,24 @@ def test_sk100_bf16_full_schedule(D):
     print(f"sk100 D={D}:", _agree(E, Eo, n_h, reps, min(E.min(), Eo.min())))
 
 
-@pytest.mark.parametrize("N,D,graph", [(256, 3, "sk"), (200, 4, "gauss")])
-def test_large_n_path_long_horizon(N, D, graph):
+@pytest.mark.parametrize("N,D,graph,prec", [(256, 3, "sk", chym.PREC_BF16X2), (200, 4, "gauss", chym.PREC_BF16X2),
+                                             (256, 3, "sk", chym.PREC_FP8)])
+def test_large_n_path_long_horizon(N, D, graph, prec):
     """The persistent large-N tensor-core kernel (N > 128) over 6000 steps, annealed
-    over the second half: SK +-1 (hi+lo products) and Gaussian J (three products,
-    energies in FP64), 4 pumps x 32 replicas."""
+    over the second half: SK +-1 (hi+lo products, BF16 and FP8 lo) and Gaussian J (three
+    products, energies in FP64), 4 pumps x 32 replicas."""
     n_h, reps, K = 4, 32, 6000
     J, eps, h, seeds = make_case(N, D, n_h, reps, 0x1A26E + N, graph)
     real = graph == "gauss"
     ctx = chym.Context(J, D, chym.J_REAL if real else chym.J_PM1)
-    prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+    prm = chym.Params(eps=eps, prec=prec)
     sch = chym.Schedule(1, K // 2, K)
     ctx.run(prm, h, seeds, K, sch)
     E = ctx.energy()
     ctx.close()
     Xo = O.run(J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm), oracle_schedule(sch), K)
     Eo = O.ising_energies(J, O.readout(Xo))
-    print(f"large N={N} D={D} {graph}:", _agree(E, Eo, n_h, reps, min(E.min(), Eo.min()), real))
+    print(f"large N={N} D={D} {graph} prec={prec}:", _agree(E, Eo, n_h, reps, min(E.min(), Eo.min()), real))
 
 
 def test_uneven_batch_instances_full_schedule():

@@ -408,6 +408,81 @@ def test_large_n_state_matches_oracle(N, D, n_h, reps, steps, graph):
     ctx.close()
 
 
+# FP8 mode: the lo half of the split in e4m3, J in e4m3 (exact for +-1).  x is then held
+# in the product within 2^-13 |x| (8 bits of the BF16 hi, 4 of the e4m3 lo), so a step's
+# coupling term eps J x is off by eps sum_q J_pq d_q with |d_q| <= 2^-13 |x_q|: about
+# eps sqrt(N) 2^-13 |x| for independent roundings (eps sqrt(N) = 1/4 here), 3e-7 |x| a
+# step after the factor dt.  Over at most 30 steps that stays near 1e-5, within the 1e-4
+# mixed-precision bound.  Real J keeps the BF16 three-term products (FP8 mode runs as
+# BF16X2 there), and so does the small-N kernel.
+FP8_CASES = [
+    # N, D, n_h, reps, steps, graph
+    (129, 4, 2, 5, 30, "sk"),
+    (200, 3, 3, 7, 30, "sk"),
+    (256, 2, 2, 40, 25, "sparse"),  # two column tiles, the second partial
+    (300, 8, 1, 9, 20, "sk"),
+    (170, 1, 2, 70, 30, "sk"),
+    (190, 6, 1, 17, 20, "sk"),
+    (1000, 4, 2, 3, 15, "sk"),
+    (2000, 8, 1, 3, 6, "sk"),
+    (150, 4, 2, 4, 20, "gauss"),    # real J: BF16 three-term products
+    (100, 4, 2, 6, 30, "sk"),       # N <= 128: the small-N kernel (BF16 hi + lo)
+]
+
+
+@pytest.mark.parametrize("N,D,n_h,reps,steps,graph", FP8_CASES)
+def test_fp8_state_matches_oracle(N, D, n_h, reps, steps, graph):
+    ctx, J, X, Xo = _run_both(N, D, n_h, reps, steps, chym.PREC_FP8, graph)
+    assert np.all(np.isfinite(X))
+    assert _rel_err(X, Xo) <= 1e-4
+    # the sign readout of the GPU's own state: exact integer energies for +-1 J, FP64
+    # sums in another order for real J
+    E, Eo = ctx.energy(), O.ising_energies(J, O.readout(X))
+    if graph == "gauss":
+        assert np.allclose(E, Eo, rtol=1e-12, atol=1e-12)
+    else:
+        assert np.array_equal(E, Eo)
+    ctx.close()
+
+
+def test_fp8_is_less_exact_than_bf16x2_but_close():
+    """FP8 mode against BF16X2 on the same seeds: the e4m3 lo half (4 bits instead of 8)
+    shows as a larger but still small state difference from the oracle."""
+    e = {}
+    for prec in (chym.PREC_BF16X2, chym.PREC_FP8):
+        ctx, J, X, Xo = _run_both(600, 4, 2, 16, 20, prec, "sk")
+        e[prec] = _rel_err(X, Xo)
+        ctx.close()
+    assert e[chym.PREC_BF16X2] < e[chym.PREC_FP8] <= 1e-4
+
+
+def test_fp8_in_a_batch_equals_alone():
+    """FP8 contexts in a batch beside BF16X2 ones: each gives the state it has alone."""
+    specs = [(inputs.sk_pm1(300, 3), 4, chym.PREC_FP8), (inputs.sk_pm1(260, 4), 4, chym.PREC_BF16X2),
+             (inputs.sk_pm1(96, 5), 3, chym.PREC_FP8)]
+
+    def make():
+        out = []
+        for k, (J, D, prec) in enumerate(specs):
+            c = chym.Context(J, D)
+            prm = chym.Params(eps=0.5 / c.lambda_max(), prec=prec)
+            sch = chym.Schedule(1, 20, 60)
+            c.run(prm, inputs.pump_grid(0.5, 2), inputs.run_seeds(71 + k, 40), 0, sch)
+            out.append((c, prm, sch))
+        return out
+
+    batched = make()
+    b = chym.Batch([c for c, _, _ in batched])
+    b.run([p for _, p, _ in batched], [s for _, _, s in batched], 36)
+    b.status()
+    b.close()
+    for (c, p, s), (ca, _, _) in zip(make(), batched):
+        c.run(p, None, None, 36, s)
+        assert np.array_equal(c.get_state()[0], ca.get_state()[0])
+        c.close()
+        ca.close()
+
+
 def test_large_n_continuation_and_energies():
     N, D, n_h, reps, K = 257, 4, 2, 6, 40
     J, eps, h, seeds = make_case(N, D, n_h, reps, 13)
