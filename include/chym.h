@@ -92,8 +92,19 @@ typedef struct {
   double kappa;    /* local saturation (kappa L) */
   double eps;      /* feedback coupling strength */
   int32_t prec;    /* chym_prec */
-  int32_t flags;   /* reserved, must be 0 */
+  int32_t flags;   /* 0, or CHYM_FLAG_TEST_STALL (tests of the timeout path only) */
 } chym_params;
+
+/* Test of the failure path of the tensor-core kernels (BF16X2/FP8 steps), nothing
+ * else: the thread that issues a step's tensor-core products withholds the signal
+ * that they are complete, so the warps that wait for them give up after their
+ * bounded wait (2 ms with this flag instead of the usual 2 s), raise the status
+ * word, drain the products they issued and free their tensor memory.  The next
+ * synchronising call (chym_energy, chym_get_state, chym_batch_status) returns
+ * CHYM_ETIMEOUT and clears the word; the state of the affected runs is then
+ * unspecified, and a following chym_run with seeds restarts them normally.  No
+ * fault, trap or unbounded wait is involved.  Paths without tensor cores ignore it. */
+#define CHYM_FLAG_TEST_STALL 1
 
 typedef struct {
   int32_t kind;     /* 0: no annealing (alpha = 1); 1: linear */

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libchym.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ESTATE = range(7)
 J_PM1, J_REAL = 0, 1
 PREC_FP64, PREC_FP32, PREC_BF16X2, PREC_FP8 = 0, 1, 2, 3
+FLAG_TEST_STALL = 1
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP", 6: "ESTATE"}
 
 EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", "chym_run",
@@ -70,10 +71,11 @@ class Params:
     kappa: float = 0.1
     eps: float = 0.05
     prec: int = PREC_FP32
+    flags: int = 0   # FLAG_TEST_STALL only in tests of the timeout path
 
     def c(self):
         return CParams(self.dt, self.sigma, self.init_std, self.gamma, self.kappa, self.eps,
-                       int(self.prec), 0)
+                       int(self.prec), int(self.flags))
 
 
 @dataclass

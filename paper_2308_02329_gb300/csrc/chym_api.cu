@@ -50,7 +50,8 @@ chym_status check_params(const chym_params* prm) {
     return fail(CHYM_EINVAL, "gamma, kappa, eps must be finite");
   if (prm->prec < CHYM_PREC_FP64 || prm->prec > CHYM_PREC_FP8)
     return fail(CHYM_EINVAL, "unknown precision");
-  if (prm->flags != 0) return fail(CHYM_EINVAL, "params.flags must be 0");
+  if (prm->flags != 0 && prm->flags != CHYM_FLAG_TEST_STALL)
+    return fail(CHYM_EINVAL, "params.flags must be 0 or CHYM_FLAG_TEST_STALL");
   return CHYM_OK;
 }
 
@@ -117,6 +118,7 @@ StepConsts make_step_consts(const chym_ctx* c, const chym_params* prm, const chy
   sc.hidx = c->d_hidx;
   sc.w = c->d_w;
   sc.fp8 = prm->prec == CHYM_PREC_FP8 ? 1 : 0;
+  sc.test_stall = (prm->flags & CHYM_FLAG_TEST_STALL) ? 1 : 0;
   return sc;
 }
 

@@ -159,7 +159,8 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     const chym_params& p = params[i];
     const chym_schedule& s = schedules[i];
     if (c->prec < 0) return fail(CHYM_ESTATE, "every context needs a state (chym_run with seeds first)");
-    if (!(p.dt > 0.0) || !(p.sigma >= 0.0) || p.flags != 0 || p.prec < CHYM_PREC_FP64 ||
+    if (!(p.dt > 0.0) || !(p.sigma >= 0.0) || (p.flags != 0 && p.flags != CHYM_FLAG_TEST_STALL) ||
+        p.prec < CHYM_PREC_FP64 ||
         p.prec > CHYM_PREC_FP8 || !isfinite(p.gamma) || !isfinite(p.kappa) || !isfinite(p.eps))
       return fail(CHYM_EINVAL, "bad params in the batch");
     if ((c->prec == CHYM_PREC_FP64) != (p.prec == CHYM_PREC_FP64))
@@ -222,6 +223,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   struct DimLaunch {
     int D, P, kp_max, terms_max;
     size_t items_off, cta_off;
+    bool stall;
   };
   std::vector<DimLaunch> dl;
   int dims_left = 0;
@@ -237,15 +239,17 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     --dims_left;
     std::vector<PlanJob> jobs;
     int kp_max = 16, terms_max = 1;
+    bool stall = false;
     for (int i : by_dim[D]) {
       jobs.push_back({desc_of[i], b->ctxs[i]->n_runs});
+      stall = stall || (params[i].flags & CHYM_FLAG_TEST_STALL);
       kp_max = std::max(kp_max, (b->ctxs[i]->N + 15) / 16 * 16);
       terms_max = std::max(terms_max, b->ctxs[i]->kind == CHYM_J_PM1 ? 1 : 2);
     }
     std::vector<unsigned char> items;
     std::vector<int> cta;
     plan_dimension(jobs, tc_chunk_runs(D), tc_runs_per_item(D), P, items, cta);
-    DimLaunch L{D, (int)cta.size() - 1, kp_max, terms_max, 0, 0};
+    DimLaunch L{D, (int)cta.size() - 1, kp_max, terms_max, 0, 0, stall};
     b->part_ctas[D] = L.P;
     b->part_units[D] = 0.0;
     for (const auto& jj : jobs) b->part_units[D] += (double)((jj.n_runs + tc_chunk_runs(D) - 1) / tc_chunk_runs(D));
@@ -278,7 +282,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
     if (b->timing) CHYM_CUDA_TRY(cudaEventRecord(b->t_begin[L.D], s));
     CHYM_CUDA_TRY(launch_tc_items(L.D, base, base + L.items_off, (const int*)(base + L.cta_off), L.P,
-                                  steps, L.kp_max, L.terms_max, b->d_status, s));
+                                  steps, L.kp_max, L.terms_max, b->d_status, s, L.stall));
     if (b->timing) {
       CHYM_CUDA_TRY(cudaEventRecord(b->t_end[L.D], s));
       b->timed[L.D] = true;

@@ -43,7 +43,12 @@ struct StepConsts {
   const int32_t* hidx;        // per run: index of its pump value in h
   const double* w;            // per spin: weight of its coupling term (nullable: all 1)
   int fp8;                    // CHYM_PREC_FP8: e4m3 lo operands on the large-N path
+  int test_stall;             // CHYM_FLAG_TEST_STALL: withhold the product completion signal
 };
+
+// Limit of every bounded device-side wait, and the short one of CHYM_FLAG_TEST_STALL.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+constexpr unsigned long long kTestWaitLimitNs = 2000000ull;
 
 // Contiguous spin ranges [begin[i], begin[i + 1]) whose Ising energies are read
 // out separately (independent graphs packed into one block-diagonal J).
@@ -157,6 +162,7 @@ struct K2Runner {
   std::vector<int> sig_dims;
   void* sig_buf = nullptr;
   int sig_cap = 0;
+  bool sig_stall = false;
   int sms = 0;
 };
 }  // namespace chym
@@ -255,7 +261,7 @@ void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out);
 void tc_fill_item(void* out, int desc, int run_begin, int run_count);
 cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, const int* d_cta_begin,
                             int n_cta, int64_t steps, int kp_max, int terms_max, unsigned* status,
-                            cudaStream_t st);
+                            cudaStream_t st, bool test_stall = false);
 cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st);
 cudaError_t launch_energy_segments(chym_ctx* c, const SegTable& t, double* d_E, cudaStream_t st);
 cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol, double bin_w,

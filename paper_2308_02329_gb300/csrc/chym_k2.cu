@@ -68,7 +68,6 @@ constexpr int kRB = 4;                         // runs of one epilogue block
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer + MMA + epilogue
 constexpr int kAccCols = 256;                  // TMEM columns of one accumulator
 constexpr size_t kRingBudget = 196 * 1024;     // shared memory for the stage ring
-constexpr int kTimeoutNs = 2000000000;
 constexpr int kGraphSteps = 16;                // steps per captured graph
 constexpr uint32_t kA8Block = 128 * kKc;       // bytes of an e4m3 A block (4 KB)
 constexpr int kLoScaleLog2 = 16;               // FP8 mode: B operands carry 2^16
@@ -90,6 +89,7 @@ struct K2Desc {
   unsigned long long buf_bytes;
   int N, KP, MT, KC, CT, RT, n, n_runs, a_terms, sched_kind;
   int lo8;                 // 1: lo half in e4m3 (FP8 mode, +-1 couplings)
+  int stall;               // CHYM_FLAG_TEST_STALL: the accumulator-full signal is withheld
   int64_t k0, k_anneal, k_total;  // k0: step of the context when the call began
   float gdt, kdt, edt, neg2ln2s2, inv_ramp;
 };
@@ -117,6 +117,7 @@ struct K2Launch {
   int stages;             // depth of the ring
   uint32_t stage_stride;  // bytes per stage
   unsigned* status;
+  unsigned long long wait_ns;  // limit of every bounded wait
 };
 
 __host__ __device__ inline uint32_t b_block_bytes(int n) { return (uint32_t)n * kKc * 2u; }
@@ -140,7 +141,7 @@ __device__ __forceinline__ uint64_t global_timer() {
 // may suspend the thread for up to kSuspendNs (it resumes as soon as the phase
 // completes), so waiting warps do not take issue slots from working ones.
 constexpr uint32_t kSuspendNs = 20000;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
     uint32_t done;
@@ -153,7 +154,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (done) return true;
     const uint64_t t = global_timer();
     if (it == 0) t0 = t;
-    else if (t - t0 > (uint64_t)kTimeoutNs) return false;
+    else if (t - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
         bool stop = false;
         for (int kc = 0; kc < KC; ++kc, ++g, a_src += kABlock, a2_src += a2, b_src += BB, bl_src += BL) {
           const uint32_t s = g % (uint32_t)S;
-          if (g >= (uint32_t)S && !mbar_wait(smem_addr(&empty_bar[s]), ((g / S) - 1u) & 1u)) {
+          if (g >= (uint32_t)S && !mbar_wait(smem_addr(&empty_bar[s]), ((g / S) - 1u) & 1u, L.wait_ns)) {
             atomicOr(L.status, STATUS_TIMEOUT);
             s_abort = 1;
             stop = true;
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
       // drain: every copy issued must have landed before the CTA may exit
       const uint32_t first = g > (uint32_t)S ? g - (uint32_t)S : 0u;
       for (uint32_t u = first; u < g; ++u)
-        if (!mbar_wait(smem_addr(&full_bar[u % S]), (u / S) & 1u)) atomicOr(L.status, STATUS_TIMEOUT);
+        if (!mbar_wait(smem_addr(&full_bar[u % S]), (u / S) & 1u, L.wait_ns)) atomicOr(L.status, STATUS_TIMEOUT);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
         const K2Desc& d = L.descs[tile.desc];
         const uint32_t BB = b_block_bytes(d.n);
         const uint32_t b = it & 1u, use = it >> 1;
-        if (use > 0 && !mbar_wait(smem_addr(&acc_empty[b]), (use - 1u) & 1u)) {
+        if (use > 0 && !mbar_wait(smem_addr(&acc_empty[b]), (use - 1u) & 1u, L.wait_ns)) {
           ok = false;
           break;
         }
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
         const int KC = d.KC;
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const uint32_t s = g % (uint32_t)S;
-          if (!mbar_wait(smem_addr(&full_bar[s]), (g / S) & 1u) || s_abort) {
+          if (!mbar_wait(smem_addr(&full_bar[s]), (g / S) & 1u, L.wait_ns) || s_abort) {
             ok = false;
             break;
           }
@@ -453,7 +454,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
           mma_commit(smem_addr(&empty_bar[s]));
         }
         if (!ok) break;
-        mma_commit(smem_addr(&acc_full[b]));
+        // (test of the timeout path: the signal is withheld, so the epilogue's wait runs
+        // out; the drain below still waits for every product issued)
+        if (!d.stall) mma_commit(smem_addr(&acc_full[b]));
       }
       if (!ok) {
         atomicOr(L.status, STATUS_TIMEOUT);
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
       }
       // every product issued must be complete before TMEM is freed
       mma_commit(smem_addr(&drain_bar));
-      if (!mbar_wait(smem_addr(&drain_bar), 0u)) atomicOr(L.status, STATUS_TIMEOUT);
+      if (!mbar_wait(smem_addr(&drain_bar), 0u, L.wait_ns)) atomicOr(L.status, STATUS_TIMEOUT);
     }
   } else {
     // ---------------- epilogue: 4 kWQ warps ----------------
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
         __syncwarp();
       }
       const uint32_t b = it & 1u;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&acc_full[b]), (it >> 1) & 1u)) &&
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&acc_full[b]), (it >> 1) & 1u, L.wait_ns)) &&
                       !s_abort;
       if (!ok) {
         if (lane == 0) {
@@ -808,6 +811,7 @@ cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void*
   d.n_runs = sc.n_runs;
   d.a_terms = c->kind == CHYM_J_PM1 ? 1 : 2;
   d.lo8 = lo8;
+  d.stall = sc.test_stall;
   d.sched_kind = sc.sched_kind;
   d.k0 = sc.k0;
   d.k_anneal = sc.k_anneal;
@@ -845,6 +849,8 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&R.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
+  bool stall = false;  // CHYM_FLAG_TEST_STALL on any context: the short wait limit
+  for (int i = 0; i < n_desc; ++i) stall = stall || reinterpret_cast<const K2Desc*>(descs.data() + i * db)->stall;
   // tile tables per dimension; ring stride per dimension
   std::vector<K2Tile> tiles;
   std::vector<int> dim_first(9, 0), dim_count(9, 0);
@@ -911,7 +917,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
       const size_t smem = std::max<size_t>((size_t)stages * dim_stride[D], 120 * 1024);
       const int grid = std::min(dim_count[D], max_ctas > 0 ? std::min(max_ctas, R.sms) : R.sms);  // as above
       K2Launch L{d_descs, d_tiles + dim_first[D], d_done, dim_count[D], k_off, stages, dim_stride[D],
-                 status};
+                 status, stall ? kTestWaitLimitNs : kWaitLimitNs};
       cudaError_t r = k2_launch(D, L, grid, smem, s);
       if (r != cudaSuccess) return r;
     }
@@ -922,7 +928,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
     // the graph stays valid while the tile table keeps its shape; the descriptor
     // contents are refreshed in place above
     const bool reuse = R.exec && R.sig_tiles == tiles.size() && R.sig_dims == dim_count &&
-                       R.sig_buf == R.d_buf && R.sig_cap == max_ctas;
+                       R.sig_buf == R.d_buf && R.sig_cap == max_ctas && R.sig_stall == stall;
     if (!reuse) {
       if (R.exec) cudaGraphExecDestroy(R.exec);
       R.exec = nullptr;
@@ -943,6 +949,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
       R.sig_dims = dim_count;
       R.sig_buf = R.d_buf;
       R.sig_cap = max_ctas;
+      R.sig_stall = stall;
     }
     for (int64_t c = 0; c < chunks; ++c) {
       e = cudaGraphLaunch(R.exec, st);

@@ -39,6 +39,7 @@ struct TcDesc {
   const int32_t* hidx;  // per run: index of its pump value
   const double* w;      // per spin: coupling weight (nullable: all 1)
   int N, KP, n_runs, replicas, a_terms, sched_kind;
+  int stall;            // CHYM_FLAG_TEST_STALL: completion of the products withheld
   int64_t k0, k_anneal, k_total;
   float dt, noise_scale, gdt, kdt, edt, inv_ramp;
 };
@@ -57,6 +58,7 @@ struct TcLaunch {
   uint32_t a_region;     // bytes reserved for the largest J image of the launch
   int kp_max;            // largest K (rows of B) of the launch
   unsigned* status;
+  unsigned long long wait_ns;  // limit of every bounded wait
 };
 
 template <int D>
@@ -69,7 +71,6 @@ struct TcCfg {
   static_assert(RG % CH == 0, "chunk must divide the group");
 };
 
-constexpr int kTimeoutNs = 2000000000;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -81,8 +82,8 @@ __device__ __forceinline__ uint64_t global_timer() {
   return t;
 }
 
-// Bounded wait for the completion of phase `parity` of an mbarrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the completion of phase `parity` of an mbarrier, for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
     uint32_t done;
@@ -97,7 +98,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if ((it & 255u) == 0u) {
       const uint64_t t = global_timer();
       if (it == 0) t0 = t;
-      else if (t - t0 > (uint64_t)kTimeoutNs) return false;
+      else if (t - t0 > limit_ns) return false;
     }
   }
 }
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
   __shared__ int s_abort;
   __shared__ __align__(8) uint64_t s_mbar[G];
   __shared__ __align__(8) uint64_t s_abar;
+  __shared__ __align__(8) uint64_t s_wh[G];  // CHYM_FLAG_TEST_STALL: where the completion goes instead
   __shared__ __align__(8) float s_ar[G][RG];
   __shared__ uint4 s_rk[G][RG][5];  // Philox round keys of each run
   __shared__ int64_t s_koff[G][RG];  // each run's (re)seeding step
@@ -341,8 +343,10 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_abar)));
-    for (int q = 0; q < G; ++q)
+    for (int q = 0; q < G; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_wh[q])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
       for (int64_t k = d.k0; k < d.k0 + L.steps; ++k) {
         if (wq == 0 && lane == 0) {
           bool ok = true;
-          if (a_pending) ok = mbar_wait(smem_addr(&s_abar), a_phase);
+          if (a_pending) ok = mbar_wait(smem_addr(&s_abar), a_phase, L.wait_ns);
           a_pending = false;
           tc_fence_after();
           if (ok) {
@@ -462,9 +466,11 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
                          idesc, 1u);
               }
             }
+            // (test of the timeout path: the completion signal goes elsewhere, so the
+            // group's wait below runs out; the drain after the loop waits for it)
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_addr(&s_mbar[g]))
+                    smem_addr(d.stall ? &s_wh[g] : &s_mbar[g]))
                 : "memory");
           } else {
             atomicOr(L.status, STATUS_TIMEOUT);
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
           }
         }
         // warp-uniform outcome: the TMEM loads below are warp-collective
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&s_mbar[g]), phase));
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&s_mbar[g]), phase, L.wait_ns));
         phase ^= 1u;
         if (!ok) {
           timed_out = true;
@@ -592,9 +598,13 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
     }
     if (wq == 0 && lane == 0) {
       // the J copy must have landed before the next item may overwrite it
-      if (a_pending) mbar_wait(smem_addr(&s_abar), a_phase);
+      if (a_pending) mbar_wait(smem_addr(&s_abar), a_phase, L.wait_ns);
       // the tensor core may still own this group's accumulator: wait once more (bounded)
-      if (timed_out) mbar_wait(smem_addr(&s_mbar[g]), phase ^ 1u);
+      // for the completion of the products of the step that timed out
+      if (timed_out) {
+        if (d.stall) mbar_wait(smem_addr(&s_wh[g]), 0u, L.wait_ns);  // the one step issued
+        else mbar_wait(smem_addr(&s_mbar[g]), phase ^ 1u, L.wait_ns);
+      }
     }
     if (new_a) {
       a_phase ^= 1u;
@@ -698,6 +708,7 @@ void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out) {
   d.n_runs = sc.n_runs;
   d.replicas = sc.replicas;
   d.a_terms = c->kind == CHYM_J_PM1 ? 1 : 2;
+  d.stall = sc.test_stall;
   d.sched_kind = sc.sched_kind;
   d.k0 = sc.k0;
   d.k_anneal = sc.k_anneal;
@@ -722,8 +733,9 @@ void tc_fill_item(void* out, int desc, int run_begin, int run_count) {
 // device memory: descs, items and the per-CTA item ranges.
 cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, const int* d_cta_begin,
                             int n_cta, int64_t steps, int kp_max, int terms_max, unsigned* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool test_stall) {
   TcLaunch L;
+  L.wait_ns = test_stall ? kTestWaitLimitNs : kWaitLimitNs;
   L.descs = (const TcDesc*)d_descs;
   L.items = (const TcItem*)d_items;
   L.cta_begin = d_cta_begin;
@@ -802,7 +814,7 @@ cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st) {
   return launch_tc_items(c->D, base, base + sizeof(TcDesc),
                          (const int*)(base + sizeof(TcDesc) + sizeof(TcItem) * n_items), n_items,
                          sc.steps, (c->N + 15) / 16 * 16, c->kind == CHYM_J_PM1 ? 1 : 2,
-                         c->d_status, st);
+                         c->d_status, st, sc.test_stall != 0);
 }
 
 }  // namespace chym
