@@ -328,6 +328,23 @@ CHYM_API chym_status chym_batch_get_tuning(chym_batch* b, double* chunk_costs, d
 CHYM_API chym_status chym_batch_set_tuning(chym_batch* b, const double* chunk_costs,
                                            const double* k2_cost);
 
+/* Tile shapes of the batch's kernels, per hyperspin dimension D = 1..8 (arrays of 8,
+ * entry D-1; 0 stands for the kernel's default): rt, the runs per column tile of the
+ * large-N path (a multiple of 32 with D rt <= 256 and D rt a multiple of 16; default
+ * 256 / 128 / 64 / 32 for D = 1 / 2 / 3-4 / 5-8, fewer for contexts with fewer runs);
+ * stages, the depth of its operand ring (2..8, capped by what its shared memory holds;
+ * default: the most that fit); chunk, the runs per epilogue chunk of the small-N path
+ * (4 or 8 for D <= 4; default 8).  chym_batch_tune chooses them by measurement after
+ * its cost-model rounds: for each D with large-N contexts every valid rt, then the
+ * three ring depths below the largest; for each D <= 4 with small-N contexts both
+ * chunks; each part keeps the shape under which it ran fastest (the whole batch runs
+ * probe_steps steps per candidate; results are unchanged by the shapes except in the
+ * order of floating-point sums).  get: outputs may be NULL; set: NULL keeps an array,
+ * EINVAL for invalid values. */
+CHYM_API chym_status chym_batch_get_shapes(chym_batch* b, int* rt, int* stages, int* chunk);
+CHYM_API chym_status chym_batch_set_shapes(chym_batch* b, const int* rt, const int* stages,
+                                           const int* chunk);
+
 CHYM_API chym_status chym_batch_destroy(chym_batch* b);
 
 /* ---- Learned early exit (no counterpart in the paper's method; a layer on top of

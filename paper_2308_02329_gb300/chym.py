@@ -30,6 +30,7 @@ EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", 
            "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
            "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
            "chym_batch_tune", "chym_batch_get_tuning", "chym_batch_set_tuning",
+           "chym_batch_get_shapes", "chym_batch_set_shapes",
            "chym_reseed_device", "chym_get_offsets_device", "chym_copy_state_device",
            "chym_features_device", "chym_mlp_create", "chym_mlp_destroy", "chym_mlp_set_params",
            "chym_mlp_get_params", "chym_mlp_forward_device", "chym_mlp_grad_device",
@@ -139,6 +140,8 @@ def lib():
         L.chym_batch_tune.argtypes = [vp, ctypes.POINTER(CParams), ctypes.POINTER(CSchedule), i64, vp]
         L.chym_batch_get_tuning.argtypes = [vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
         L.chym_batch_set_tuning.argtypes = [vp, vp, vp]
+        L.chym_batch_get_shapes.argtypes = [vp, vp, vp, vp]
+        L.chym_batch_set_shapes.argtypes = [vp, vp, vp, vp]
         L.chym_stats_noalloc.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(CStats), vp, vp,
                                          i32, vp]
         for name in EXPORTS:
@@ -399,17 +402,32 @@ class Batch:
         _check(lib().chym_batch_status(self._h))
 
     def tuning(self):
-        """The planner's cost model: {"chunk": [D=1..8], "k2": float, "tuned": bool}."""
+        """The planner's cost model and tile shapes: {"chunk": [D=1..8], "k2": float,
+        "tuned": bool, "shapes": {"rt": [...], "stages": [...], "ch": [...]}} (shape 0: the
+        kernel's default)."""
         c = (ctypes.c_double * 8)()
         k2 = ctypes.c_double()
         t = ctypes.c_int32()
         _check(lib().chym_batch_get_tuning(self._h, c, ctypes.byref(k2), ctypes.byref(t)))
-        return {"chunk": list(c), "k2": k2.value, "tuned": bool(t.value)}
+        return {"chunk": list(c), "k2": k2.value, "tuned": bool(t.value), "shapes": self.shapes()}
 
     def set_tuning(self, tuning):
         c = (ctypes.c_double * 8)(*tuning["chunk"])
         k2 = ctypes.c_double(tuning["k2"])
         _check(lib().chym_batch_set_tuning(self._h, c, ctypes.byref(k2)))
+        if "shapes" in tuning:
+            self.set_shapes(tuning["shapes"])
+
+    def shapes(self):
+        """Tile shapes per D = 1..8: large-N runs per column tile ("rt") and ring depth
+        ("stages"), small-N epilogue chunk ("ch"); 0 stands for the kernel's default."""
+        rt, st, ch = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)()
+        _check(lib().chym_batch_get_shapes(self._h, rt, st, ch))
+        return {"rt": list(rt), "stages": list(st), "ch": list(ch)}
+
+    def set_shapes(self, shapes):
+        arr = [(ctypes.c_int32 * 8)(*shapes[k]) if k in shapes else None for k in ("rt", "stages", "ch")]
+        _check(lib().chym_batch_set_shapes(self._h, *arr))
 
     def signature(self, device_key=""):
         """Key of the batch's composition for a tuning cache."""
@@ -436,7 +454,7 @@ class Batch:
         _check(lib().chym_batch_tune(self._h, P, S, int(probe_steps), ctypes.c_void_p(stream)))
         out = self.tuning()
         if cache_path:
-            cache[key] = {"chunk": out["chunk"], "k2": out["k2"]}
+            cache[key] = {"chunk": out["chunk"], "k2": out["k2"], "shapes": out["shapes"]}
             tmp = cache_path + ".tmp"
             with open(tmp, "w") as f:
                 json.dump(cache, f, indent=1, sort_keys=True)

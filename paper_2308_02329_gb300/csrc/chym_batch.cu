@@ -40,6 +40,9 @@ struct chym_batch {
   double chunk_cost[9] = {0, 1.10, 0.64, 0.91, 1.01, 1.27, 1.43, 1.60, 1.76};
   double k2_cost = 1.05;
   bool tuned = false;
+  // Tile shapes (0: the kernels' defaults), chosen by chym_batch_tune's search or set by
+  // the caller: large-N runs per column tile and ring depth, small-N epilogue chunk.
+  chym::TileShapes shapes;
   // Timing of the parts of a run (used by the tuner): index D = 1..8 for the small-N
   // launch of dimension D, 0 for the large-N launches; their CTAs and work units.
   bool timing = false;
@@ -202,7 +205,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
   for (int i = 0; i < n; ++i) {
     const chym_ctx* c = b->ctxs[i];
     if (is_tc_prec(params[i].prec) && c->N > 128 && !uses_csr(c, params[i].prec))
-      total += b->k2_cost * (double)k2_work_units(c->N, c->D, c->n_runs);
+      total += b->k2_cost * (double)k2_work_units(c->N, c->D, c->n_runs, b->shapes.rt[c->D]);
   }
   // SMs for the small-N dimensions (all of them when there is no large-N work)
   const int sms_small = small_total > 0.0
@@ -282,7 +285,8 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
     CHYM_CUDA_TRY(cudaStreamWaitEvent(s, b->fork, 0));
     if (b->timing) CHYM_CUDA_TRY(cudaEventRecord(b->t_begin[L.D], s));
     CHYM_CUDA_TRY(launch_tc_items(L.D, base, base + L.items_off, (const int*)(base + L.cta_off), L.P,
-                                  steps, L.kp_max, L.terms_max, b->d_status, s, L.stall));
+                                  steps, L.kp_max, L.terms_max, b->d_status, s, L.stall,
+                                  b->shapes.ch[L.D]));
     if (b->timing) {
       CHYM_CUDA_TRY(cudaEventRecord(b->t_end[L.D], s));
       b->timed[L.D] = true;
@@ -304,7 +308,7 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
       c->prec = params[i].prec;
       descs.resize(descs.size() + kb);
       const StepConsts sc = make_step_consts(c, &params[i], &schedules[i], c->k, steps);
-      cudaError_t e = k2_prepare(c, sc, s, descs.data() + descs.size() - kb);
+      cudaError_t e = k2_prepare(c, sc, s, descs.data() + descs.size() - kb, b->shapes.rt[c->D]);
       if (e != cudaSuccess) return cuda_fail(e, "large-N preparation");
       dims.push_back(c->D);
       idx.push_back(i);
@@ -316,9 +320,11 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
       const int cap = small_ctas > 0 ? std::max(1, b->sms - small_ctas) : 0;
       b->part_ctas[0] = cap > 0 ? cap : b->sms;
       b->part_units[0] = 0.0;
-      for (int i : idx) b->part_units[0] += (double)k2_work_units(b->ctxs[i]->N, b->ctxs[i]->D, b->ctxs[i]->n_runs);
+      for (int i : idx)
+        b->part_units[0] += (double)k2_work_units(b->ctxs[i]->N, b->ctxs[i]->D, b->ctxs[i]->n_runs,
+                                                  b->shapes.rt[b->ctxs[i]->D]);
       if (b->timing) CHYM_CUDA_TRY(cudaEventRecord(b->t_begin[0], s));
-      cudaError_t e = k2_integrate(b->k2, descs, dims, steps, b->d_status, s, cap);
+      cudaError_t e = k2_integrate(b->k2, descs, dims, steps, b->d_status, s, cap, b->shapes.stages);
       if (b->timing && e == cudaSuccess) {
         CHYM_CUDA_TRY(cudaEventRecord(b->t_end[0], s));
         b->timed[0] = true;
@@ -452,6 +458,82 @@ CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
       else b->chunk_cost[p] = c;
     }
   }
+  // ---- tile shapes: coordinate search, one part at a time, at the tuned split ----
+  // Each candidate runs the whole batch for probe_steps steps (timed per part); a part
+  // keeps the candidate under which its own time was shortest.  Large-N parts (one per
+  // dimension, timed together): runs per column tile, then ring depth; small-N parts:
+  // the epilogue chunk.  Changing one part's shape leaves the others' work unchanged.
+  if (status == CHYM_OK) {
+    for (int D = 0; D <= 8; ++D) b->chunk_cost[D] = best_chunk[D];
+    b->k2_cost = best_k2;
+    auto probe = [&](int part, double* t_out) -> chym_status {
+      chym_status r = chym_batch_run(b, params, schedules, probe_steps, st);
+      if (r != CHYM_OK) return r;
+      cudaError_t ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) return cuda_fail(ce, "chym_batch_tune: shape probe");
+      r = chym_batch_status(b);
+      if (r != CHYM_OK) return r;
+      float ms = 0.f;
+      if (!b->timed[part]) return fail(CHYM_ESTATE, "chym_batch_tune: part not timed");
+      ce = cudaEventElapsedTime(&ms, b->t_begin[part], b->t_end[part]);
+      if (ce != cudaSuccess) return cuda_fail(ce, "chym_batch_tune: timing");
+      *t_out = (double)ms;
+      return CHYM_OK;
+    };
+    bool large[9] = {}, small[9] = {};
+    int terms[9] = {}, lo8[9] = {}, runs[9] = {};
+    for (int i = 0; i < n; ++i) {
+      const chym_ctx* c = b->ctxs[i];
+      if (!is_tc_prec(params[i].prec) || uses_csr(c, params[i].prec)) continue;
+      if (c->N <= 128) {
+        small[c->D] = true;
+      } else {
+        large[c->D] = true;
+        terms[c->D] = std::max(terms[c->D], c->kind == CHYM_J_PM1 ? 1 : 2);
+        lo8[c->D] = lo8[c->D] || (params[i].prec == CHYM_PREC_FP8 && c->kind == CHYM_J_PM1);
+        runs[c->D] = std::max(runs[c->D], c->n_runs);
+      }
+    }
+    b->timing = true;
+    for (int D = 1; D <= 8 && status == CHYM_OK; ++D) {
+      if (!large[D]) continue;
+      double best = INFINITY;
+      int best_rt = b->shapes.rt[D];
+      for (int rt = 32; rt <= 256 && status == CHYM_OK; rt *= 2) {
+        if (!k2_rt_valid(D, rt) || (rt > 32 && rt / 2 >= runs[D])) continue;
+        b->shapes.rt[D] = rt;
+        double t = 0.0;
+        status = probe(0, &t);
+        if (status == CHYM_OK && t < best) {
+          best = t;
+          best_rt = rt;
+        }
+      }
+      b->shapes.rt[D] = best_rt;
+      const int smax = k2_max_stages(D, best_rt, runs[D], terms[D], lo8[D]);
+      int best_s = 0;  // the most that fit
+      for (int sg = smax - 1; sg >= std::max(2, smax - 3) && status == CHYM_OK; --sg) {
+        b->shapes.stages[D] = sg;
+        double t = 0.0;
+        status = probe(0, &t);
+        if (status == CHYM_OK && t < best) {
+          best = t;
+          best_s = sg;
+        }
+      }
+      b->shapes.stages[D] = best_s;
+    }
+    for (int D = 1; D <= 4 && status == CHYM_OK; ++D) {
+      if (!small[D]) continue;
+      double t8 = 0.0, t4 = 0.0;
+      b->shapes.ch[D] = 8;
+      status = probe(D, &t8);
+      if (status != CHYM_OK) break;
+      b->shapes.ch[D] = 4;
+      status = probe(D, &t4);
+      b->shapes.ch[D] = t4 < t8 ? 4 : 8;
+    }
+  }
   b->timing = false;
   // restore the states
   for (int i = 0; i < n; ++i) {
@@ -468,6 +550,7 @@ CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
   release();
   for (int D = 0; D <= 8; ++D) b->chunk_cost[D] = best_chunk[D];
   b->k2_cost = best_k2;
+  if (status != CHYM_OK) b->shapes = TileShapes();
   if (status != CHYM_OK) return status;
   b->tuned = true;
   return CHYM_OK;
@@ -495,6 +578,34 @@ CHYM_API chym_status chym_batch_set_tuning(chym_batch* b, const double* chunk_co
     for (int D = 0; D < 8; ++D) b->chunk_cost[D + 1] = chunk_costs[D];
   if (k2_cost) b->k2_cost = *k2_cost;
   if (chunk_costs || k2_cost) b->tuned = true;
+  return CHYM_OK;
+}
+
+CHYM_API chym_status chym_batch_get_shapes(chym_batch* b, int* rt, int* stages, int* chunk) {
+  if (!b) return fail(CHYM_EINVAL, "NULL batch");
+  for (int D = 0; D < 8; ++D) {
+    if (rt) rt[D] = b->shapes.rt[D + 1];
+    if (stages) stages[D] = b->shapes.stages[D + 1];
+    if (chunk) chunk[D] = b->shapes.ch[D + 1];
+  }
+  return CHYM_OK;
+}
+
+CHYM_API chym_status chym_batch_set_shapes(chym_batch* b, const int* rt, const int* stages, const int* chunk) {
+  if (!b) return fail(CHYM_EINVAL, "NULL batch");
+  for (int D = 1; D <= 8; ++D) {
+    if (rt && rt[D - 1] != 0 && !k2_rt_valid(D, rt[D - 1]))
+      return fail(CHYM_EINVAL, "runs per column tile: 0, or a multiple of 32 with D rt <= 256");
+    if (stages && stages[D - 1] != 0 && (stages[D - 1] < 2 || stages[D - 1] > 8))
+      return fail(CHYM_EINVAL, "ring stages: 0, or 2..8");
+    if (chunk && chunk[D - 1] != 0 && !(D <= 4 && (chunk[D - 1] == 4 || chunk[D - 1] == 8)))
+      return fail(CHYM_EINVAL, "epilogue chunk: 0, or 4 or 8 for D <= 4");
+  }
+  for (int D = 1; D <= 8; ++D) {
+    if (rt) b->shapes.rt[D] = rt[D - 1];
+    if (stages) b->shapes.stages[D] = stages[D - 1];
+    if (chunk) b->shapes.ch[D] = chunk[D - 1];
+  }
   return CHYM_OK;
 }
 

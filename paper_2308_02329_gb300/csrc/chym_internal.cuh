@@ -163,6 +163,7 @@ struct K2Runner {
   void* sig_buf = nullptr;
   int sig_cap = 0;
   bool sig_stall = false;
+  std::vector<int> sig_stages;
   int sms = 0;
 };
 }  // namespace chym
@@ -239,16 +240,19 @@ cudaError_t launch_step_simt(chym_ctx* c, const StepConsts& sc, int32_t prec, cu
 cudaError_t launch_step_tc(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 cudaError_t launch_step_k2(chym_ctx* c, const StepConsts& sc, cudaStream_t st);
 // large-N path over several contexts (chym_k2.cu)
-cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void* desc_out);
+cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void* desc_out, int rt = 0);
+// most ring stages of the large-N kernel for a context of dimension D with rt runs per
+// column tile (0: the default), real J (terms 2) or FP8 lo, within its shared memory
+int k2_max_stages(int D, int rt, int n_runs, int a_terms, int lo8);
 size_t k2_desc_bytes();
 // tiles x K chunks of one step of a large-N context (the planner's work unit)
-long long k2_work_units(int N, int D, int n_runs);
+long long k2_work_units(int N, int D, int n_runs, int rt = 0);
 cudaError_t k2_finish(chym_ctx* c, const void* desc, cudaStream_t st);
 // max_ctas > 0 caps the persistent grid (the SMs left to the large-N path when the
 // small-N kernels of a batch occupy the others).
 cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
                          const std::vector<int>& dims, int64_t steps, unsigned* status,
-                         cudaStream_t st, int max_ctas = 0);
+                         cudaStream_t st, int max_ctas = 0, const int* stages = nullptr);
 void k2_runner_release(K2Runner& R);
 // small-N tensor-core kernel over an item plan (chym_tc.cu)
 cudaError_t prepare_tc_operand(chym_ctx* c);
@@ -261,7 +265,18 @@ void tc_fill_desc(const chym_ctx* c, const StepConsts& sc, void* out);
 void tc_fill_item(void* out, int desc, int run_begin, int run_count);
 cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, const int* d_cta_begin,
                             int n_cta, int64_t steps, int kp_max, int terms_max, unsigned* status,
-                            cudaStream_t st, bool test_stall = false);
+                            cudaStream_t st, bool test_stall = false, int chunk = 0);
+// Tile shapes the batch autotuner may choose (0: the kernels' defaults).
+struct TileShapes {
+  int rt[9] = {};      // large-N path: runs per column tile, per D
+  int stages[9] = {};  // large-N path: depth of the operand ring, per D
+  int ch[9] = {};      // small-N path: runs per epilogue chunk, per D (4 or 8 for D <= 4)
+};
+// valid choices of the large-N runs per column tile for dimension D (a multiple of 32,
+// D RT <= 256 and a multiple of 16)
+inline bool k2_rt_valid(int D, int rt) {
+  return rt >= 32 && rt % 32 == 0 && D * rt <= 256 && (D * rt) % 16 == 0;
+}
 cudaError_t launch_energy(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st);
 cudaError_t launch_energy_segments(chym_ctx* c, const SegTable& t, double* d_E, cudaStream_t st);
 cudaError_t launch_stats(chym_ctx* c, const double* d_E, double E_gs, double tol, double bin_w,

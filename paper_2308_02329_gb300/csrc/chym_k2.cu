@@ -726,19 +726,27 @@ cudaError_t k2_launch(int D, const K2Launch& L, int grid, size_t smem, cudaStrea
   return cudaErrorInvalidValue;
 }
 
-// Runs per column tile of a context: the most for its D, shrunk (in multiples of
-// 32) for contexts with fewer runs so that small instances waste no columns.
-int k2_rt(int D, int n_runs) {
+// Runs per column tile of a context: the most for its D (or the autotuner's choice
+// `want`), shrunk (in multiples of 32) for contexts with fewer runs so that small
+// instances waste no columns.
+int k2_rt(int D, int n_runs, int want = 0) {
   const int r32 = (n_runs + 31) / 32 * 32;
-  return std::min(k2_rt_max(D), std::max(32, r32));
+  const int top = want > 0 && k2_rt_valid(D, want) ? want : k2_rt_max(D);
+  return std::min(top, std::max(32, r32));
 }
 
 }  // namespace
 
-long long k2_work_units(int N, int D, int n_runs) {
+int k2_max_stages(int D, int rt, int n_runs, int a_terms, int lo8) {
+  const int n = D * k2_rt(D, n_runs, rt);
+  const uint32_t stride = (stage_bytes(n, a_terms, lo8) + 1023u) / 1024u * 1024u;
+  return (int)std::min<size_t>(kMaxStages, std::max<size_t>(2, kRingBudget / stride));
+}
+
+long long k2_work_units(int N, int D, int n_runs, int rt) {
   if (D < 1 || D > 8) return 0;
   const long long MT = (N + 127) / 128, K64 = 2 * MT;  // K in units of 64 spins
-  const int RT = k2_rt(D, n_runs);
+  const int RT = k2_rt(D, n_runs, rt);
   const long long CT = (n_runs + RT - 1) / RT;
   return MT * CT * K64 * (long long)(D * RT) / 128;  // in 128-column tile units
 }
@@ -763,12 +771,12 @@ cudaError_t prepare_k2_operand(chym_ctx* c) {
 // Runner: a set of large-N contexts integrated together for `steps` steps.
 // ---------------------------------------------------------------------------
 // Workspace, per-run constants and buffer 0 of one context; fills its descriptor.
-cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void* desc_out) {
+cudaError_t k2_prepare(chym_ctx* c, const StepConsts& sc, cudaStream_t st, void* desc_out, int rt) {
   cudaError_t e = prepare_k2_operand(c);
   if (e != cudaSuccess) return e;
   K2Desc& d = *reinterpret_cast<K2Desc*>(desc_out);
   const int N = c->N, D = c->D, MT = (N + 127) / 128, KP = MT * 128, KC = KP / kKc;
-  const int RT = k2_rt(D, sc.n_runs), n = D * RT;
+  const int RT = k2_rt(D, sc.n_runs, rt), n = D * RT;
   const int CT = (sc.n_runs + RT - 1) / RT;
   const int lo8 = sc.fp8 && c->kind == CHYM_J_PM1 ? 1 : 0;
   const size_t BB = b_block_bytes(n), BL = b_lo_bytes(n, lo8);
@@ -839,7 +847,7 @@ cudaError_t k2_finish(chym_ctx* c, const void* desc, cudaStream_t st) {
 // replayed.
 cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
                          const std::vector<int>& dims, int64_t steps, unsigned* status,
-                         cudaStream_t st, int max_ctas) {
+                         cudaStream_t st, int max_ctas, const int* stage_choice) {
   const size_t db = sizeof(K2Desc);
   const int n_desc = (int)dims.size();
   cudaError_t e = cudaSuccess;
@@ -908,11 +916,18 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
   e = cudaMemcpyAsync(base, blob.data(), bytes, cudaMemcpyHostToDevice, st);  // also zeroes *done
   if (e != cudaSuccess) return e;
 
+  // ring depth per dimension: as many stages as the ring budget holds, or fewer when
+  // the autotuner chose so
+  std::vector<int> dim_stages(9, 0);
+  for (int D = 1; D <= 8; ++D) {
+    if (!dim_count[D]) continue;
+    dim_stages[D] = (int)std::min<size_t>(kMaxStages, std::max<size_t>(2, kRingBudget / dim_stride[D]));
+    if (stage_choice && stage_choice[D] >= 2) dim_stages[D] = std::min(dim_stages[D], stage_choice[D]);
+  }
   auto issue = [&](int k_off, cudaStream_t s) -> cudaError_t {
     for (int D = 1; D <= 8; ++D) {
       if (!dim_count[D]) continue;
-      const int stages =
-          (int)std::min<size_t>(kMaxStages, std::max<size_t>(2, kRingBudget / dim_stride[D]));
+      const int stages = dim_stages[D];
       // at least 120 KB: one CTA (which owns 512 TMEM columns) per SM
       const size_t smem = std::max<size_t>((size_t)stages * dim_stride[D], 120 * 1024);
       const int grid = std::min(dim_count[D], max_ctas > 0 ? std::min(max_ctas, R.sms) : R.sms);  // as above
@@ -928,7 +943,8 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
     // the graph stays valid while the tile table keeps its shape; the descriptor
     // contents are refreshed in place above
     const bool reuse = R.exec && R.sig_tiles == tiles.size() && R.sig_dims == dim_count &&
-                       R.sig_buf == R.d_buf && R.sig_cap == max_ctas && R.sig_stall == stall;
+                       R.sig_buf == R.d_buf && R.sig_cap == max_ctas && R.sig_stall == stall &&
+                       R.sig_stages == dim_stages;
     if (!reuse) {
       if (R.exec) cudaGraphExecDestroy(R.exec);
       R.exec = nullptr;
@@ -950,6 +966,7 @@ cudaError_t k2_integrate(K2Runner& R, const std::vector<unsigned char>& descs,
       R.sig_buf = R.d_buf;
       R.sig_cap = max_ctas;
       R.sig_stall = stall;
+      R.sig_stages = dim_stages;
     }
     for (int64_t c = 0; c < chunks; ++c) {
       e = cudaGraphLaunch(R.exec, st);

@@ -61,11 +61,13 @@ struct TcLaunch {
   unsigned long long wait_ns;  // limit of every bounded wait
 };
 
-template <int D>
+// CH_ = 0: the default runs per epilogue chunk (8 for D <= 4, else 4); the batch
+// autotuner may choose 4 for D <= 4.
+template <int D, int CH_ = 0>
 struct TcCfg {
   static constexpr int RG = D == 1 ? 64 : D == 2 ? 32 : (D == 6 || D == 8) ? 8 : 16;
   static constexpr int CG = D * RG;        // MMA N: columns of one group
-  static constexpr int CH = D <= 4 ? 8 : 4;  // runs per epilogue chunk
+  static constexpr int CH = CH_ ? CH_ : D <= 4 ? 8 : 4;  // runs per epilogue chunk
   static constexpr int G = std::min(4, 512 / (2 * CG));
   static_assert(CG % 16 == 0 && CG <= 256, "MMA N must be a multiple of 16 in [16, 256]");
   static_assert(RG % CH == 0, "chunk must divide the group");
@@ -311,9 +313,9 @@ __device__ __forceinline__ void quad_transpose(float v0, float v1, float v2, flo
   b[3] = high ? ko : ro;
 }
 
-template <int D>
+template <int D, int CH_>
 __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
-  using Cfg = TcCfg<D>;
+  using Cfg = TcCfg<D, CH_>;
   constexpr int RG = Cfg::RG, CG = Cfg::CG, CH = Cfg::CH, G = Cfg::G;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint32_t s_tmem;
@@ -657,15 +659,15 @@ float bf16_value(uint16_t b) {
   return f;
 }
 
-template <int D>
+template <int D, int CH_>
 cudaError_t launch_tc_plan(const TcLaunch& L, int n_cta, cudaStream_t st) {
-  using Cfg = TcCfg<D>;
+  using Cfg = TcCfg<D, CH_>;
   const size_t b_bytes = (size_t)L.kp_max * Cfg::CG * 2u;
   // at least 128 KB: one CTA owns all 512 TMEM columns of its SM, so neither a
   // second CTA of this kernel nor a large-N step CTA (>= 104 KB) may be placed
   // beside it (it would wait in tcgen05.alloc until this CTA exits)
   const size_t smem = std::max<size_t>(L.a_region + (size_t)Cfg::G * 2 * b_bytes, 128 * 1024);
-  auto kern = step_tc_kernel<D>;
+  auto kern = step_tc_kernel<D, CH_>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n_cta, 128 * Cfg::G, smem, st>>>(L);
@@ -733,7 +735,7 @@ void tc_fill_item(void* out, int desc, int run_begin, int run_count) {
 // device memory: descs, items and the per-CTA item ranges.
 cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, const int* d_cta_begin,
                             int n_cta, int64_t steps, int kp_max, int terms_max, unsigned* status,
-                            cudaStream_t st, bool test_stall) {
+                            cudaStream_t st, bool test_stall, int chunk) {
   TcLaunch L;
   L.wait_ns = test_stall ? kTestWaitLimitNs : kWaitLimitNs;
   L.descs = (const TcDesc*)d_descs;
@@ -744,14 +746,14 @@ cudaError_t launch_tc_items(int D, const void* d_descs, const void* d_items, con
   L.a_region = (uint32_t)(terms_max * 128 * kp_max * 2);
   L.status = status;
   switch (D) {
-    case 1: return launch_tc_plan<1>(L, n_cta, st);
-    case 2: return launch_tc_plan<2>(L, n_cta, st);
-    case 3: return launch_tc_plan<3>(L, n_cta, st);
-    case 4: return launch_tc_plan<4>(L, n_cta, st);
-    case 5: return launch_tc_plan<5>(L, n_cta, st);
-    case 6: return launch_tc_plan<6>(L, n_cta, st);
-    case 7: return launch_tc_plan<7>(L, n_cta, st);
-    case 8: return launch_tc_plan<8>(L, n_cta, st);
+    case 1: return chunk == 4 ? launch_tc_plan<1, 4>(L, n_cta, st) : launch_tc_plan<1, 0>(L, n_cta, st);
+    case 2: return chunk == 4 ? launch_tc_plan<2, 4>(L, n_cta, st) : launch_tc_plan<2, 0>(L, n_cta, st);
+    case 3: return chunk == 4 ? launch_tc_plan<3, 4>(L, n_cta, st) : launch_tc_plan<3, 0>(L, n_cta, st);
+    case 4: return chunk == 4 ? launch_tc_plan<4, 4>(L, n_cta, st) : launch_tc_plan<4, 0>(L, n_cta, st);
+    case 5: return launch_tc_plan<5, 0>(L, n_cta, st);
+    case 6: return launch_tc_plan<6, 0>(L, n_cta, st);
+    case 7: return launch_tc_plan<7, 0>(L, n_cta, st);
+    case 8: return launch_tc_plan<8, 0>(L, n_cta, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -639,13 +639,65 @@ def test_batch_tuning_keeps_states_and_results(tmp_path):
     other = chym.Batch(ctxs)
     other.set_tuning({"chunk": [1.0] * 8, "k2": 1.0})
     t2 = other.tune(prms, schs, probe_steps=12, cache_path=cache)
-    assert t2["chunk"] == t["chunk"] and t2["k2"] == t["k2"]
+    assert t2["chunk"] == t["chunk"] and t2["k2"] == t["k2"] and t2["shapes"] == t["shapes"]
+    # the chosen tile shapes are valid ones (0: default) for the batch's dimensions
+    for D in range(1, 9):
+        rt, st, ch = (t["shapes"][k][D - 1] for k in ("rt", "stages", "ch"))
+        assert rt == 0 or (rt % 32 == 0 and D * rt <= 256)
+        assert st == 0 or 2 <= st <= 8
+        assert ch in (0, 4, 8)
     with pytest.raises(chym.ChymError):
         other.set_tuning({"chunk": [1.0] * 7 + [0.0], "k2": 1.0})
     other.close()
     batch.close()
     for c in ctxs:
         c.close()
+
+
+def test_batch_tile_shapes_leave_results_unchanged():
+    """Every tile shape the autotuner may choose (large-N runs per column tile and ring
+    depth, small-N epilogue chunk) computes the same arithmetic per element in the same
+    order: states are bit-identical to the default shapes; invalid shapes are refused."""
+    cases = [(100, 2, 4, 20, "mobius"), (60, 3, 4, 9, "sk"), (90, 4, 2, 20, "sk"), (40, 1, 2, 40, "sk"),
+             (300, 4, 4, 16, "sk"), (611, 2, 2, 40, "sk"), (200, 3, 2, 40, "gauss"), (250, 1, 2, 80, "sk")]
+    K = 24
+
+    def run(shapes):
+        ctxs, prms, schs = [], [], []
+        for i, (N, D, n_h, reps, graph) in enumerate(cases):
+            J, eps, h, seeds = make_case(N, D, n_h, reps, 170 + i, graph)
+            c = chym.Context(J, D, chym.J_REAL if graph == "gauss" else chym.J_PM1)
+            prm = chym.Params(eps=eps, prec=chym.PREC_BF16X2)
+            sch = chym.Schedule(1, 10, K)
+            c.run(prm, h, seeds, 0, sch)
+            ctxs.append(c)
+            prms.append(prm)
+            schs.append(sch)
+        b = chym.Batch(ctxs)
+        if shapes:
+            b.set_shapes(shapes)
+            assert b.shapes() == shapes
+        b.run(prms, schs, K)
+        b.status()
+        out = [c.get_state()[0] for c in ctxs]
+        b.close()
+        for c in ctxs:
+            c.close()
+        return out
+
+    ref = run(None)
+    for shapes in ({"rt": [32] * 8, "stages": [2] * 8, "ch": [4, 4, 4, 4, 0, 0, 0, 0]},
+                   {"rt": [128, 64, 32, 32, 32, 32, 32, 32], "stages": [3] * 8, "ch": [8, 8, 8, 8, 0, 0, 0, 0]}):
+        for a, b in zip(ref, run(shapes)):
+            assert np.array_equal(a, b)
+    c = chym.Context(inputs.sk_pm1(20, 1), 2)
+    b = chym.Batch([c])
+    for bad in ({"rt": [48] + [0] * 7}, {"rt": [0, 0, 0, 128, 0, 0, 0, 0]}, {"stages": [1] + [0] * 7},
+                {"ch": [0] * 4 + [4] + [0] * 3}, {"ch": [6] + [0] * 7}):
+        with pytest.raises(chym.ChymError):
+            b.set_shapes(bad)
+    b.close()
+    c.close()
 
 
 def test_uneven_batch_full_size_sampled():
