@@ -315,10 +315,12 @@ def replay_against_oracle(jobs, steps):
         glob = float(np.max(np.abs(Xo)))
         scale = np.maximum(np.max(np.abs(Xo), axis=1, keepdims=True), 1e-12 * glob)
         err = np.max(np.abs(X - Xo) / scale, axis=(1, 2))
+        # exact integers for +-1 couplings; FP64 sums in another order for real J
+        same = (E == Eo) if j["name"] != "gauss" else np.isclose(E, Eo, rtol=1e-12, atol=1e-12)
         out[j["name"]] = {"runs": REPLAY_RUNS, "steps": steps, "of_steps": j["sched"].k_total,
                           "state_rel_err_max": float(err.max()),
                           "state_rel_err_median": float(np.median(err)),
-                          "energy_equal_frac": float(np.mean(E == Eo)),
+                          "energy_equal_frac": float(np.mean(same)),
                           "oracle_seconds": el}
     return out
 
