@@ -89,6 +89,24 @@ def test_large_n_path_long_horizon(N, D, graph, prec):
     print(f"large N={N} D={D} {graph} prec={prec}:", _agree(E, Eo, n_h, reps, min(E.min(), Eo.min()), real))
 
 
+@pytest.mark.parametrize("prec", [chym.PREC_BF16X2, chym.PREC_FP8])
+def test_large_n_512_statistics(prec):
+    """SK +-1 N = 512, D = 4 (the size class of the N = 800 and 1000 workloads, at an
+    oracle cost of seconds): 4 pumps x 16 replicas over 3000 steps, annealed over the
+    second half; pooled success and mean energy above the best energy reached."""
+    N, D, n_h, reps, K = 512, 4, 4, 16, 3000
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 0x5120 + prec)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=eps, prec=prec)
+    sch = chym.Schedule(1, K // 2, K)
+    ctx.run(prm, h, seeds, K, sch)
+    E = ctx.energy()
+    ctx.close()
+    Xo = O.run(J, D, inputs.h_per_run(h, reps), seeds, oracle_params(prm), oracle_schedule(sch), K)
+    Eo = O.ising_energies(J, O.readout(Xo))
+    print(f"N=512 prec={prec}:", _agree(E, Eo, 1, n_h * reps, min(E.min(), Eo.min())))
+
+
 def test_uneven_batch_instances_full_schedule():
     """Instances of the batched uneven workload (SK +-1, 16 pumps x 4 replicas each, the
     benchmark's constants: D = 2 as the XY machine without annealing, D >= 3 annealed
