@@ -258,6 +258,24 @@ chym_status chym_create(const double* J, int N, int D, chym_jkind kind, chym_ctx
   }
   if (e == cudaSuccess) e = cudaMemcpy(c->d_J8, j8.data(), nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+  if (e == cudaSuccess && kind == CHYM_J_PM1) {  // bit planes of the Ising energy
+    const int W = (N + 63) / 64;
+    std::vector<uint64_t> planes((size_t)2 * W * N, 0ull);
+    std::vector<int32_t> deg(N, 0);
+    for (int p = 0; p < N; ++p)
+      for (int q = 0; q < N; ++q) {
+        const double v = J[(size_t)p * N + q];
+        if (v == 0.0) continue;
+        const size_t at = (size_t)(v > 0.0 ? 0 : W) * N + (size_t)(q / 64) * N + p;
+        planes[at] |= 1ull << (q % 64);
+        deg[p] += v > 0.0 ? 1 : -1;
+      }
+    e = cudaMalloc((void**)&c->d_Jbits, planes.size() * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_jdeg, sizeof(int32_t) * N);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_Jbits, planes.data(), planes.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_jdeg, deg.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice);
+  }
   // sparse J: compressed rows for the CUDA-core product
   size_t nz = 0;
   for (size_t i = 0; i < nn; ++i) nz += J[i] != 0.0;
@@ -308,6 +326,8 @@ chym_status chym_destroy(chym_ctx* c) {
   free_dev(c->d_J32);
   free_dev(c->d_J32p);
   free_dev(c->d_J8);
+  free_dev(c->d_Jbits);
+  free_dev(c->d_jdeg);
   free_dev(c->d_Jbf16);
   free_dev(c->d_X);
   free_dev(c->d_h);

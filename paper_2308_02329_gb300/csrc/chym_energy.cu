@@ -32,15 +32,23 @@ __device__ V block_sum(V v, V* red) {
   return t;  // valid in thread 0
 }
 
-// One CTA per run.  J is symmetric, so thread p reads J[q][p] (coalesced).
+// One CTA per run.  Real J: thread p reads J[q][p] (J symmetric: coalesced), FP64.
+// +-1 J: bit planes of J, plane[w][p] = the bits of row p's columns 64 w .. 64 w + 63
+// where J = +1 (Jpos) or -1 (Jneg), word-major so that consecutive rows are coalesced.
+// With d_p = the spins that differ from s_p (one xor of the spin words),
+//   sum_q J_pq s_p s_q = deg_p - 2 (popc(Jpos_p & d_p) - popc(Jneg_p & d_p)),
+// deg_p = (#J = +1) - (#J = -1) in row p: an exact integer from N/64 words a row.
+constexpr int kMaxSpinWords = 64;  // N <= 4096
 template <typename T, bool PM1>
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(
-    const T* __restrict__ X, int N, int D, const int8_t* __restrict__ J8,
+    const T* __restrict__ X, int N, int D, const uint64_t* __restrict__ Jpos,
+    const uint64_t* __restrict__ Jneg, const int32_t* __restrict__ deg,
     const double* __restrict__ J64, double* __restrict__ E, uint64_t* __restrict__ spins) {
   extern __shared__ int8_t s[];
   __shared__ int bad;
   __shared__ long long red_i[32];
   __shared__ double red_d[32];
+  __shared__ uint64_t sw[kMaxSpinWords];
   const int run = blockIdx.x, tid = threadIdx.x;
   if (tid == 0) bad = 0;
   __syncthreads();
@@ -53,21 +61,25 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(
   }
   if (my_bad) atomicOr(&bad, 1);
   __syncthreads();
-  if (spins) {
-    const int words = (N + 63) / 64;
-    for (int w = tid; w < words; w += blockDim.x) {
-      uint64_t bits = 0;
-      for (int b = 0; b < 64 && 64 * w + b < N; ++b)
-        if (s[64 * w + b] > 0) bits |= (1ull << b);
-      spins[(size_t)run * words + w] = bits;
-    }
+  const int words = (N + 63) / 64;
+  for (int w = tid; w < words; w += blockDim.x) {
+    uint64_t bits = 0;
+    for (int b = 0; b < 64 && 64 * w + b < N; ++b)
+      if (s[64 * w + b] > 0) bits |= (1ull << b);
+    sw[w] = bits;
+    if (spins) spins[(size_t)run * words + w] = bits;
   }
+  __syncthreads();
   if (PM1) {
     long long acc = 0;
     for (int p = tid; p < N; p += blockDim.x) {
-      int f = 0;
-      for (int q = 0; q < N; ++q) f += (int)J8[(size_t)q * N + p] * (int)s[q];
-      acc += (long long)s[p] * f;
+      const uint64_t flip = s[p] > 0 ? ~0ull : 0ull;  // d = spins unlike s_p (padding bits meet no J)
+      int c = 0;
+      for (int w = 0; w < words; ++w) {
+        const uint64_t d = sw[w] ^ flip;
+        c += __popcll(__ldg(Jpos + (size_t)w * N + p) & d) - __popcll(__ldg(Jneg + (size_t)w * N + p) & d);
+      }
+      acc += (long long)(deg[p] - 2 * c);
     }
     const long long tot = block_sum<long long>(acc, red_i);
     if (tid == 0) E[run] = bad ? (double)NAN : -(double)tot;
@@ -212,12 +224,14 @@ template <typename T>
 cudaError_t launch_energy_typed(chym_ctx* c, double* d_E, uint64_t* d_spins, cudaStream_t st) {
   const T* X = (const T*)c->d_X;
   const size_t smem = (size_t)c->N;
+  if (c->N > 64 * kMaxSpinWords) return cudaErrorInvalidValue;
+  const int W = (c->N + 63) / 64;
   if (c->kind == CHYM_J_PM1)
-    energy_kernel<T, true><<<c->n_runs, kEnergyThreads, smem, st>>>(X, c->N, c->D, c->d_J8,
-                                                                     c->d_J64, d_E, d_spins);
+    energy_kernel<T, true><<<c->n_runs, kEnergyThreads, smem, st>>>(
+        X, c->N, c->D, c->d_Jbits, c->d_Jbits + (size_t)W * c->N, c->d_jdeg, c->d_J64, d_E, d_spins);
   else
-    energy_kernel<T, false><<<c->n_runs, kEnergyThreads, smem, st>>>(X, c->N, c->D, c->d_J8,
-                                                                      c->d_J64, d_E, d_spins);
+    energy_kernel<T, false><<<c->n_runs, kEnergyThreads, smem, st>>>(
+        X, c->N, c->D, nullptr, nullptr, nullptr, c->d_J64, d_E, d_spins);
   return cudaGetLastError();
 }
 

@@ -180,6 +180,10 @@ struct chym_ctx {
   float* d_J32p = nullptr;    // FP32 N x j32p_ld, rows zero padded to a multiple of 4
   int j32p_ld = 0;
   int8_t* d_J8 = nullptr;     // int8 N x N (+-1/0 couplings only)
+  // +-1 couplings: bit planes for the Ising energy, [plane][word w][row p] (plane 0: J = +1,
+  // plane 1: J = -1; word w holds columns 64 w .. 64 w + 63), and per row (#+1) - (#-1)
+  uint64_t* d_Jbits = nullptr;
+  int32_t* d_jdeg = nullptr;
   // J in compressed rows when it is sparse (at most N^2 / 16 nonzeros): the coupling
   // product then runs on the CUDA cores over the nonzeros only
   bool sparse = false;
