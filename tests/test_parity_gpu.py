@@ -427,6 +427,7 @@ FP8_CASES = [
     (2000, 8, 1, 3, 6, "sk"),
     (150, 4, 2, 4, 20, "gauss"),    # real J: BF16 three-term products
     (100, 4, 2, 6, 30, "sk"),       # N <= 128: the small-N kernel (BF16 hi + lo)
+    (4096, 2, 1, 2, 4, "sk"),       # the largest N
 ]
 
 
