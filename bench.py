@@ -281,6 +281,16 @@ def step_roofline(jobs, prec, steps_total, dur, clock_info, peaks, peak_src, pre
                          "integer multiply counts 2 (half-rate pipe), frac_unweighted counts it 1"}
 
 
+# DRAM bytes (read + write) of the dominant kernel per launch, from ncu captures of these
+# kernels as they stand (dram__bytes_read.sum + dram__bytes_write.sum), by workload and
+# precision: None where no capture of the current kernel exists.
+TRAFFIC = {
+    ("n100", "bf16x2"): (3.22e7, "the three step_tc_kernel launches of one bench step (D = 2, 3, 4; "
+                                 "6.9 + 11.1 + 14.2 MB read, writes stay in L2)"),
+    ("sk800", "fp8"): (2.972e9, "one step_k2_kernel launch (one integration step): 1486 MB captured "
+                                "on 32768 runs, doubled for 65536 (traffic grows with the columns)"),
+}
+
 REPLAY_RUNS, REPLAY_STEPS = 64, 400
 
 
@@ -903,6 +913,8 @@ def measure(args, w, sim_steps, rank, world, local, warm_steps=None, replay=Fals
     peaks, peak_src = measured_peaks()
     roofline = step_roofline(jobs, prec, args.steps * sim_steps, dur, clock_info, peaks, peak_src,
                              args.prec)
+    if (w.key, args.prec) in TRAFFIC and sim_steps == w.steps and not args.replicas:
+        roofline["traffic"], roofline["traffic_note"] = TRAFFIC[(w.key, args.prec)]
 
     # ---------------- the plain FP32 form on the same workload ----------------
     plain = None
