@@ -221,6 +221,24 @@ __device__ __forceinline__ void box_muller(uint32_t wr, uint32_t wa, float neg2l
   z0 = r * c;
   z1 = r * s;
 }
+// The same transform for the word pairs of two runs at once, in paired FP32 arithmetic
+// (identical roundings): z0 = (z0 of run A, of run B), likewise z1.
+__device__ __forceinline__ void box_muller2(uint32_t wrA, uint32_t waA, uint32_t wrB, uint32_t waB,
+                                            float neg2ln2s2, float2& z0, float2& z1) {
+  const float2 ur = __ffma2_rn(make_float2((float)wrA, (float)wrB),
+                               make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f),
+                               make_float2(1.1641532182693481e-10f, 1.1641532182693481e-10f));
+  const float2 th = __ffma2_rn(make_float2((float)waA, (float)waB),
+                               make_float2(1.4629180792671596e-09f, 1.4629180792671596e-09f),
+                               make_float2(-3.1415926528582302f, -3.1415926528582302f));
+  const float2 r2 = __fmul2_rn(make_float2(neg2ln2s2, neg2ln2s2), make_float2(lg2_ftz(ur.x), lg2_ftz(ur.y)));
+  const float2 r = make_float2(-sqrt_ftz(r2.x), -sqrt_ftz(r2.y));
+  float sA, cA, sB, cB;
+  sincos_ftz(th.x, sA, cA);
+  sincos_ftz(th.y, sB, cB);
+  z0 = __fmul2_rn(r, make_float2(cA, cB));
+  z1 = __fmul2_rn(r, make_float2(sA, sB));
+}
 // Philox4x32-10 (the generator of chym_internal.cuh) with each round's two
 // products as 32 x 32 -> 64-bit multiplies.
 __device__ __forceinline__ uint4 philox_wide(uint4 c, uint32_t k0, uint32_t k1) {
@@ -555,34 +573,42 @@ __global__ void __launch_bounds__(kThreads, 1) step_k2_kernel(K2Launch L) {
           if (M == 4) tmem_ld4x2(c0 + 2u * (uint32_t)RT, c0 + 3u * (uint32_t)RT, y[2], y[3]);
           else if (M == 3) tmem_ld4(c0 + 2u * (uint32_t)RT, y[2]);
 #pragma unroll
-          for (int j = 0; j < kRB; ++j) {
-            const RunC c = rcb[j];
-            const bool ok_run = live && run0 + j < n_runs;
-            float z[4];
+          for (int j = 0; j < kRB; j += 2) {  // two runs at once, paired FP32 arithmetic
+            const RunC cA = rcb[j], cB = rcb[j + 1];
+            const bool okA = live && run0 + j < n_runs, okB = live && run0 + j + 1 < n_runs;
+            float2 z[4];
             if constexpr (D <= 2) {
               // the 4/D spins with the same p / (4/D) share one block; spin p takes its
               // normals (p % (4/D)) D .. + D - 1, one Box-Muller pair
               constexpr uint32_t per = 4u / D;
-              const uint4 w = philox_wide(make_uint4((uint32_t)p / per, 0u, c.kl_lo, c.kl_hi), c.key0, c.key1);
+              const uint4 wA = philox_wide(make_uint4((uint32_t)p / per, 0u, cA.kl_lo, cA.kl_hi), cA.key0, cA.key1);
+              const uint4 wB = philox_wide(make_uint4((uint32_t)p / per, 0u, cB.kl_lo, cB.kl_hi), cB.key0, cB.key1);
               const uint32_t j0 = ((uint32_t)p % per) * D;
-              float cz, sz;
-              box_muller(j0 >= 2u ? w.z : w.x, j0 >= 2u ? w.w : w.y, nl2, cz, sz);
+              const bool hi2 = j0 >= 2u;
+              float2 cz, sz;
+              box_muller2(hi2 ? wA.z : wA.x, hi2 ? wA.w : wA.y, hi2 ? wB.z : wB.x, hi2 ? wB.w : wB.y, nl2, cz, sz);
               z[0] = (j0 & 1u) ? sz : cz;
               z[1] = sz;
             } else {
-              const uint4 w = philox_wide(make_uint4((uint32_t)p, (uint32_t)blk, c.kl_lo, c.kl_hi), c.key0, c.key1);
-              box_muller(w.x, w.y, nl2, z[0], z[1]);
-              if (M > 2) box_muller(w.z, w.w, nl2, z[2], z[3]);
+              const uint4 wA = philox_wide(make_uint4((uint32_t)p, (uint32_t)blk, cA.kl_lo, cA.kl_hi), cA.key0, cA.key1);
+              const uint4 wB = philox_wide(make_uint4((uint32_t)p, (uint32_t)blk, cB.kl_lo, cB.kl_hi), cB.key0, cB.key1);
+              box_muller2(wA.x, wA.y, wB.x, wB.y, nl2, z[0], z[1]);
+              if (M > 2) box_muller2(wA.z, wA.w, wB.z, wB.w, nl2, z[2], z[3]);
             }
+            const float2 t2 = make_float2(tl[j], tl[j + 1]), nk2 = make_float2(-kdt, -kdt);
+            const float2 e0 = make_float2(edt, edt), e1 = make_float2(cA.erp, cB.erp);
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
               if (m < M) {
                 const int mu = 4 * blk + m;
-                const float xv = xc[mu][j];
-                const float s = fmaf(-kdt * xv, xv, tl[j]);
-                const float v = fmaf(xv, s, fmaf(mu == 0 ? edt : c.erp, y[m][j], z[m]));
-                xc[mu][j] = ok_run ? v : 0.f;
-                if (ok_run) __stcs(xrow + (j * D + mu) * KP, v);
+                const float2 xv = make_float2(xc[mu][j], xc[mu][j + 1]);
+                const float2 sf = __ffma2_rn(__fmul2_rn(nk2, xv), xv, t2);
+                const float2 inner = __ffma2_rn(mu == 0 ? e0 : e1, make_float2(y[m][j], y[m][j + 1]), z[m]);
+                const float2 v = __ffma2_rn(xv, sf, inner);
+                xc[mu][j] = okA ? v.x : 0.f;
+                xc[mu][j + 1] = okB ? v.y : 0.f;
+                if (okA) __stcs(xrow + (j * D + mu) * KP, v.x);
+                if (okB) __stcs(xrow + ((j + 1) * D + mu) * KP, v.y);
               }
             }
           }
