@@ -236,6 +236,21 @@ CHYM_API chym_status chym_set_state(chym_ctx* ctx, const double* X, int n_runs, 
                            int n_h, const uint64_t* seeds, int64_t k, int32_t prec,
                            void* cuda_stream);
 
+/* Checkpoint of the complete run state of ctx into a host buffer: the state in its
+ * storage precision (bit-exact), the step k, the pumps h, and per run its noise key,
+ * (re)seeding step and pump index, behind a header (format version 1, N, D, n_runs,
+ * n_h, precision).  The noise is counter based, so restoring and continuing equals
+ * continuing the original, reseeded runs included (the paper's runs are integrated over
+ * up to 1.5e5 round trips each, text before Fig. 4).  With buf NULL, *len gets the size
+ * needed; otherwise *len is the buffer's size (EINVAL if too small) and gets the size
+ * written.  ESTATE without a state.  Synchronises the stream. */
+CHYM_API chym_status chym_checkpoint(chym_ctx* ctx, void* buf, size_t* len, void* cuda_stream);
+
+/* Restore a checkpoint written by chym_checkpoint into ctx, which must have the same N
+ * and D (EINVAL otherwise, and for a buffer whose header or size does not match); the
+ * context then continues exactly where the checkpointed one was.  Synchronises. */
+CHYM_API chym_status chym_restore(chym_ctx* ctx, const void* buf, size_t len, void* cuda_stream);
+
 /* Retire-and-reseed: the n runs listed in d_runs (device int32) restart from the
  * new seeds d_new_seeds (device, n keys) at their local step 0 while the other
  * runs continue: x(0) = init_std * N(0,1) from the new key (tag 1), and from then

@@ -30,7 +30,7 @@ EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", 
            "chym_ground_state_mobius", "chym_ground_state_search", "chym_stats_noalloc",
            "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
            "chym_batch_tune", "chym_batch_get_tuning", "chym_batch_set_tuning",
-           "chym_batch_get_shapes", "chym_batch_set_shapes",
+           "chym_batch_get_shapes", "chym_batch_set_shapes", "chym_checkpoint", "chym_restore",
            "chym_reseed_device", "chym_get_offsets_device", "chym_copy_state_device",
            "chym_features_device", "chym_mlp_create", "chym_mlp_destroy", "chym_mlp_set_params",
            "chym_mlp_get_params", "chym_mlp_forward_device", "chym_mlp_grad_device",
@@ -141,6 +141,8 @@ def lib():
         L.chym_batch_get_tuning.argtypes = [vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
         L.chym_batch_set_tuning.argtypes = [vp, vp, vp]
         L.chym_batch_get_shapes.argtypes = [vp, vp, vp, vp]
+        L.chym_checkpoint.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t), vp]
+        L.chym_restore.argtypes = [vp, vp, ctypes.c_size_t, vp]
         L.chym_batch_set_shapes.argtypes = [vp, vp, vp, vp]
         L.chym_stats_noalloc.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(CStats), vp, vp,
                                          i32, vp]
@@ -221,6 +223,18 @@ class Context:
         _check(lib().chym_run_device(self._h, ctypes.byref(params.c()), ctypes.c_void_p(d_h),
                                      int(n_h), ctypes.c_void_p(d_seeds), int(n_runs), int(steps),
                                      ctypes.byref(schedule.c()), ctypes.c_void_p(stream)))
+
+    def checkpoint(self, stream=0):
+        """The complete run state as bytes (chym_checkpoint)."""
+        n = ctypes.c_size_t(0)
+        _check(lib().chym_checkpoint(self._h, None, ctypes.byref(n), ctypes.c_void_p(stream)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().chym_checkpoint(self._h, buf, ctypes.byref(n), ctypes.c_void_p(stream)))
+        return buf.raw[: n.value]
+
+    def restore(self, data, stream=0):
+        """Continue from bytes written by checkpoint() (chym_restore)."""
+        _check(lib().chym_restore(self._h, data, len(data), ctypes.c_void_p(stream)))
 
     def info(self):
         n_runs, n_h, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()

@@ -608,4 +608,96 @@ chym_status chym_set_state(chym_ctx* c, const double* X, int n_runs, const doubl
   return CHYM_OK;
 }
 
+// ---- checkpoint / restore: the complete run state in one host buffer ----
+namespace {
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t N, D, n_runs, n_h, prec;
+  int64_t k;
+  uint64_t x_bytes;
+};
+constexpr char kCkptMagic[8] = {'C', 'H', 'Y', 'M', 'C', 'K', 'P', 'T'};
+size_t ckpt_bytes(int n_runs, int n_h, size_t x_bytes) {
+  return sizeof(CkptHeader) + x_bytes + sizeof(double) * n_h +
+         (sizeof(uint64_t) + sizeof(int64_t) + sizeof(int32_t)) * (size_t)n_runs;
+}
+}  // namespace
+
+chym_status chym_checkpoint(chym_ctx* c, void* buf, size_t* len, void* stream) {
+  chym::TraceRange trace_("chym_checkpoint");
+  if (!c || !len) return fail(CHYM_EINVAL, "NULL argument");
+  if (c->prec < 0) return fail(CHYM_ESTATE, "no state");
+  const size_t xb = (size_t)c->n_runs * c->N * c->D * (c->prec == CHYM_PREC_FP64 ? 8 : 4);
+  const size_t need = ckpt_bytes(c->n_runs, c->n_h, xb);
+  if (!buf) {
+    *len = need;
+    return CHYM_OK;
+  }
+  if (*len < need) return fail(CHYM_EINVAL, "checkpoint buffer too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  CkptHeader hd;
+  memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.N = c->N;
+  hd.D = c->D;
+  hd.n_runs = c->n_runs;
+  hd.n_h = c->n_h;
+  hd.prec = c->prec;
+  hd.k = c->k;
+  hd.x_bytes = xb;
+  unsigned char* b = (unsigned char*)buf;
+  memcpy(b, &hd, sizeof(hd));
+  unsigned char* o = b + sizeof(hd);
+  CHYM_CUDA_TRY(cudaMemcpyAsync(o, c->d_X, xb, cudaMemcpyDeviceToHost, st));
+  o += xb;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(o, c->d_h, sizeof(double) * c->n_h, cudaMemcpyDeviceToHost, st));
+  o += sizeof(double) * c->n_h;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(o, c->d_seeds, sizeof(uint64_t) * c->n_runs, cudaMemcpyDeviceToHost, st));
+  o += sizeof(uint64_t) * c->n_runs;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(o, c->d_koff, sizeof(int64_t) * c->n_runs, cudaMemcpyDeviceToHost, st));
+  o += sizeof(int64_t) * c->n_runs;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(o, c->d_hidx, sizeof(int32_t) * c->n_runs, cudaMemcpyDeviceToHost, st));
+  CHYM_CUDA_TRY(cudaStreamSynchronize(st));
+  *len = need;
+  return check_device_status(c);
+}
+
+chym_status chym_restore(chym_ctx* c, const void* buf, size_t len, void* stream) {
+  chym::TraceRange trace_("chym_restore");
+  if (!c || !buf) return fail(CHYM_EINVAL, "NULL argument");
+  CkptHeader hd;
+  if (len < sizeof(hd)) return fail(CHYM_EINVAL, "checkpoint too short");
+  memcpy(&hd, buf, sizeof(hd));
+  if (memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1)
+    return fail(CHYM_EINVAL, "not a checkpoint of this library");
+  if (hd.N != c->N || hd.D != c->D) return fail(CHYM_EINVAL, "checkpoint of another N or D");
+  if (hd.n_h < 1 || hd.n_runs < 1 || hd.n_runs % hd.n_h || hd.k < 0 || hd.prec < CHYM_PREC_FP64 ||
+      hd.prec > CHYM_PREC_FP8)
+    return fail(CHYM_EINVAL, "corrupt checkpoint header");
+  const size_t xb = (size_t)hd.n_runs * c->N * c->D * (hd.prec == CHYM_PREC_FP64 ? 8 : 4);
+  if (hd.x_bytes != xb || len < ckpt_bytes(hd.n_runs, hd.n_h, xb))
+    return fail(CHYM_EINVAL, "checkpoint size does not match its header");
+  chym_status s = ensure_batch(c, hd.n_runs, hd.n_h);
+  if (s != CHYM_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned char* o = (const unsigned char*)buf + sizeof(hd);
+  CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_X, o, xb, cudaMemcpyHostToDevice, st));
+  o += xb;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_h, o, sizeof(double) * hd.n_h, cudaMemcpyHostToDevice, st));
+  o += sizeof(double) * hd.n_h;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_seeds, o, sizeof(uint64_t) * hd.n_runs, cudaMemcpyHostToDevice, st));
+  o += sizeof(uint64_t) * hd.n_runs;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_koff, o, sizeof(int64_t) * hd.n_runs, cudaMemcpyHostToDevice, st));
+  o += sizeof(int64_t) * hd.n_runs;
+  CHYM_CUDA_TRY(cudaMemcpyAsync(c->d_hidx, o, sizeof(int32_t) * hd.n_runs, cudaMemcpyHostToDevice, st));
+  CHYM_CUDA_TRY(cudaStreamSynchronize(st));
+  c->n_runs = hd.n_runs;
+  c->n_h = hd.n_h;
+  c->prec = hd.prec;
+  c->k = hd.k;
+  c->have_energy = false;
+  return CHYM_OK;
+}
+
 }  // extern "C"

@@ -145,6 +145,46 @@ def test_checkpoint_resume_is_bit_identical():
     b.close()
 
 
+@pytest.mark.parametrize("N,D,prec", [(40, 4, chym.PREC_FP64), (100, 3, chym.PREC_BF16X2),
+                                      (200, 2, chym.PREC_FP8), (60, 5, chym.PREC_FP32)])
+def test_checkpoint_restore_continues_bit_identically(N, D, prec):
+    """chym_checkpoint / chym_restore carry the whole run state (storage-precision state,
+    step, pumps, and per run key, seeding step and pump index): runs that were retired and
+    reseeded mid-way continue in a fresh context exactly as in the original."""
+    torch = pytest.importorskip("torch")
+    n_h, reps, K1, K2 = 2, 6, 30, 25
+    J, eps, h, seeds = make_case(N, D, n_h, reps, 23 + N)
+    prm = chym.Params(eps=eps, prec=prec)
+    sch = chym.Schedule(1, 20, 80)
+    a = chym.Context(J, D)
+    a.run(prm, h, seeds, K1, sch)
+    runs = torch.tensor([1, 4, 9], dtype=torch.int32, device="cuda")
+    new_seeds = torch.from_numpy(inputs.run_seeds(991, 3).view(np.int64)).cuda()
+    new_pump = torch.tensor([1, 0, 1], dtype=torch.int32, device="cuda")
+    a.reseed_device(runs.data_ptr(), 3, new_seeds.data_ptr(), prm.init_std, new_pump.data_ptr())
+    a.run(prm, None, None, 7, sch, n_runs=len(seeds))
+    blob = a.checkpoint()
+    b = chym.Context(J, D)
+    b.restore(blob)
+    assert b.info() == a.info()
+    a.run(prm, None, None, K2, sch, n_runs=len(seeds))
+    b.run(prm, None, None, K2, sch, n_runs=len(seeds))
+    Xa, ka = a.get_state()
+    Xb, kb = b.get_state()
+    assert ka == kb == K1 + 7 + K2 and np.array_equal(Xa, Xb)
+    assert np.array_equal(a.energy(), b.energy())
+    # a checkpoint of another size or a damaged header is refused
+    c = chym.Context(inputs.sk_pm1(N + 1, 1), D)
+    with pytest.raises(chym.ChymError):
+        c.restore(blob)
+    with pytest.raises(chym.ChymError):
+        b.restore(b"XXXXXXXX" + blob[8:])
+    with pytest.raises(chym.ChymError):
+        b.restore(blob[:-8])
+    for ctx in (a, b, c):
+        ctx.close()
+
+
 def test_stats_match_oracle_figures_of_merit():
     N, D, n_h, reps = 16, 2, 4, 16
     J, eps, h, seeds = make_case(N, D, n_h, reps, 5)
