@@ -412,6 +412,20 @@ CHYM_API chym_status chym_mlp_train_step_device(chym_mlp* net, const float* d_fe
                                                 const float* d_labels, int B, float lr,
                                                 float* d_loss, void* cuda_stream);
 
+/* One decision pass of continuous operation with the learned early exit: for every run
+ * at the context's current step k, with its local step l = k - offset (see
+ * chym_reseed_device): done = l >= K; hit = done and |E - E_gs| <= 1e-9 max(1, |E_gs|)
+ * (d_E: the runs' energies, device doubles, e.g. from chym_energy_device); at_dec = l ==
+ * k_dec where d_logits (device float, nullable) is given; retire = at_dec and logit <
+ * theta; restart = done or retire.  d_counts (device int64, 5): the numbers of at_dec,
+ * retire, done, hit and restart runs.  d_order (device int32, n_runs): the restarted
+ * runs in increasing order, then the others in increasing order (the first `restart`
+ * entries are the list chym_reseed_device takes).  K >= 1.  Asynchronous. */
+CHYM_API chym_status chym_exit_scan_device(chym_ctx* ctx, const double* d_E, double E_gs,
+                                           const float* d_logits, float theta, int64_t K,
+                                           int64_t k_dec, long long* d_counts, int32_t* d_order,
+                                           void* cuda_stream);
+
 /* ---- Statistics without device allocation ----
  * No counterpart in the paper: this entry point exists for callers that cannot
  * allocate device memory at the point where they need the statistics (a host

@@ -31,6 +31,7 @@ EXPORTS = ["chym_last_error", "chym_create", "chym_destroy", "chym_lambda_max", 
            "chym_batch_create", "chym_batch_run", "chym_batch_status", "chym_batch_destroy",
            "chym_batch_tune", "chym_batch_get_tuning", "chym_batch_set_tuning",
            "chym_batch_get_shapes", "chym_batch_set_shapes", "chym_checkpoint", "chym_restore",
+           "chym_exit_scan_device",
            "chym_reseed_device", "chym_get_offsets_device", "chym_copy_state_device",
            "chym_features_device", "chym_mlp_create", "chym_mlp_destroy", "chym_mlp_set_params",
            "chym_mlp_get_params", "chym_mlp_forward_device", "chym_mlp_grad_device",
@@ -143,6 +144,8 @@ def lib():
         L.chym_batch_get_shapes.argtypes = [vp, vp, vp, vp]
         L.chym_checkpoint.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t), vp]
         L.chym_restore.argtypes = [vp, vp, ctypes.c_size_t, vp]
+        L.chym_exit_scan_device.argtypes = [vp, vp, dbl, vp, ctypes.c_float, ctypes.c_int64,
+                                            ctypes.c_int64, vp, vp, vp]
         L.chym_batch_set_shapes.argtypes = [vp, vp, vp, vp]
         L.chym_stats_noalloc.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(CStats), vp, vp,
                                          i32, vp]
@@ -319,6 +322,15 @@ class Context:
 
     def offsets_device(self, d_out, stream=0):
         _check(lib().chym_get_offsets_device(self._h, ctypes.c_void_p(d_out), ctypes.c_void_p(stream)))
+
+    def exit_scan_device(self, d_E, E_gs, d_logits, theta, K, k_dec, d_counts, d_order, stream=0):
+        """One decision pass of continuous operation (chym_exit_scan_device): device
+        addresses d_E (float64), d_logits (float32 or 0), d_counts (int64[5]), d_order
+        (int32[n_runs])."""
+        _check(lib().chym_exit_scan_device(self._h, ctypes.c_void_p(d_E), float(E_gs),
+                                           ctypes.c_void_p(d_logits or None), float(theta), int(K),
+                                           int(k_dec), ctypes.c_void_p(d_counts),
+                                           ctypes.c_void_p(d_order), ctypes.c_void_p(stream)))
 
     def copy_state_device(self, d_dst, stream=0):
         _check(lib().chym_copy_state_device(self._h, ctypes.c_void_p(d_dst), ctypes.c_void_p(stream)))

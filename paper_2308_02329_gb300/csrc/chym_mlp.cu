@@ -445,7 +445,87 @@ size_t grad_smem() {
 }
 }  // namespace
 
+namespace chym {
+namespace {
+// One decision pass of continuous operation, one CTA: thread t owns the runs
+// [t n / T, (t + 1) n / T) in order, so an exclusive scan of the per-thread restart counts
+// gives every restarted run its place in the increasing list.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) exit_scan_kernel(
+    const int64_t* __restrict__ koff, int n, int64_t k, const double* __restrict__ E, double E_gs,
+    double tol, const float* __restrict__ logits, float theta, int64_t K, int64_t k_dec,
+    long long* __restrict__ counts, int32_t* __restrict__ restart) {
+  __shared__ int s_cnt[kScanThreads];
+  __shared__ long long s_sum[5][32];
+  const int t = threadIdx.x;
+  const int b = (int)((int64_t)t * n / kScanThreads), e = (int)((int64_t)(t + 1) * n / kScanThreads);
+  long long c_dec = 0, c_ret = 0, c_done = 0, c_hit = 0;
+  int c_rs = 0;
+  for (int r = b; r < e; ++r) {
+    const int64_t l = k - koff[r];
+    const bool done = l >= K;
+    const bool at_dec = logits != nullptr && l == k_dec;
+    const bool retire = at_dec && logits[r] < theta;
+    c_dec += at_dec;
+    c_ret += retire;
+    c_done += done;
+    c_hit += done && fabs(E[r] - E_gs) <= tol;
+    c_rs += done || retire;
+  }
+  s_cnt[t] = c_rs;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {  // inclusive scan (Hillis-Steele)
+    const int v = t >= o ? s_cnt[t - o] : 0;
+    __syncthreads();
+    s_cnt[t] += v;
+    __syncthreads();
+  }
+  int at = s_cnt[t] - c_rs;  // exclusive prefix
+  for (int r = b; r < e; ++r) {
+    const int64_t l = k - koff[r];
+    const bool restart_r = l >= K || (logits != nullptr && l == k_dec && logits[r] < theta);
+    if (restart_r) restart[at++] = r;
+  }
+  // the other runs after the restarted ones, in increasing order (a full permutation)
+  const int total = s_cnt[kScanThreads - 1];
+  int keep = total + (b - (s_cnt[t] - c_rs));
+  for (int r = b; r < e; ++r) {
+    const int64_t l = k - koff[r];
+    const bool restart_r = l >= K || (logits != nullptr && l == k_dec && logits[r] < theta);
+    if (!restart_r) restart[keep++] = r;
+  }
+  long long v[5] = {c_dec, c_ret, c_done, c_hit, (long long)c_rs};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    long long x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((t & 31) == 0) s_sum[i][t >> 5] = x;
+  }
+  __syncthreads();
+  if (t < 5) {
+    long long x = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) x += s_sum[t][w];
+    counts[t] = x;
+  }
+}
+}  // namespace
+}  // namespace chym
+
 extern "C" {
+
+CHYM_API chym_status chym_exit_scan_device(chym_ctx* c, const double* d_E, double E_gs,
+                                           const float* d_logits, float theta, int64_t K,
+                                           int64_t k_dec, long long* d_counts, int32_t* d_order,
+                                           void* stream) {
+  if (!c || !d_E || !d_counts || !d_order) return fail(CHYM_EINVAL, "NULL argument");
+  if (c->prec < 0) return fail(CHYM_ESTATE, "no state");
+  if (K < 1 || k_dec < 0 || !isfinite(E_gs)) return fail(CHYM_EINVAL, "bad K, k_dec or E_gs");
+  const double tol = 1e-9 * fmax(1.0, fabs(E_gs));
+  exit_scan_kernel<<<1, kScanThreads, 0, (cudaStream_t)stream>>>(
+      c->d_koff, c->n_runs, c->k, d_E, E_gs, tol, d_logits, theta, K, k_dec, d_counts, d_order);
+  CHYM_CUDA_TRY(cudaGetLastError());
+  return CHYM_OK;
+}
 
 CHYM_API chym_status chym_copy_state_device(chym_ctx* c, void* d_dst, void* stream) {
   if (!c || !d_dst) return fail(CHYM_EINVAL, "NULL argument");

@@ -173,10 +173,12 @@ def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, c
             ctx.run(prm, h, ss.take(R), 0, sched, stream)
             dt = torch.float64 if prm.prec == chym.PREC_FP64 else torch.float32
             per.append(dict(
-                next_h=0, offs=torch.zeros(R, dtype=torch.int64, device="cuda"),
+                next_h=0, order=torch.empty(R, dtype=torch.int32, device="cuda"),
                 snap=torch.empty(ctx.N * ctx.D * R, dtype=dt, device="cuda"),
                 F=torch.empty(R, chym.N_FEATURES, dtype=torch.float32, device="cuda"),
+                L=torch.empty(R, dtype=torch.float32, device="cuda"),
                 E=torch.empty(R, dtype=torch.float64, device="cuda")))
+        counts_d = torch.zeros(n, 5, dtype=torch.int64, device="cuda")
         R_all = sum(Rs)
         up_seeds = torch.empty(R_all, dtype=torch.int64).pin_memory()
         up_pumps = torch.empty(R_all, dtype=torch.int32).pin_memory()
@@ -212,28 +214,22 @@ def continuous_many(ctxs, prms, scheds, hs, Rs, seed_streams, K, k_dec, E_gss, c
                 advance(k_dec - k_dec // 2)
             else:
                 advance(k_dec)
-            counts, orders = [], []
             for i in range(n):
                 ctx, R, st = ctxs[i], Rs[i], per[i]
                 out.run_steps += R * k_dec
-                ctx.offsets_device(st["offs"].data_ptr(), stream)
-                local = ctx.info()[2] - st["offs"]
-                done = local >= K
                 ctx.energy_device(st["E"].data_ptr(), 0, stream)
-                hit = done & ((st["E"] - E_gss[i]).abs() <= 1e-9 * max(1.0, abs(E_gss[i])))
-                at_dec = local == k_dec
-                retire = torch.zeros_like(done)
+                d_logits = 0
                 if gated[i]:
                     ctx.features_device(st["snap"].data_ptr(), k_dec / K, st["F"].data_ptr(), stream)
-                    retire = at_dec & (logits(net, st["F"], stream) < thetas[i])
-                else:
-                    at_dec = torch.zeros_like(done)
-                restart = done | retire
-                counts.append(torch.stack([at_dec.sum(), retire.sum(), done.sum(), hit.sum(),
-                                           restart.sum()]))
-                # restarted slots first, in increasing slot order
-                orders.append(torch.argsort((~restart).to(torch.int8), stable=True).to(torch.int32))
-            c = torch.stack(counts).cpu().numpy()   # the chunk's one meeting with the host
+                    net.forward_device(st["F"].data_ptr(), R, st["L"].data_ptr(), stream)
+                    d_logits = st["L"].data_ptr()
+                # the decision pass on the device: counts, and the restarted slots first in
+                # increasing slot order
+                ctx.exit_scan_device(st["E"].data_ptr(), E_gss[i], d_logits,
+                                     thetas[i] if gated[i] else 0.0, K, k_dec,
+                                     counts_d[i].data_ptr(), st["order"].data_ptr(), stream)
+            orders = [st["order"] for st in per]
+            c = counts_d.cpu().numpy()   # the chunk's one meeting with the host
             base, todo = 0, []
             for i in range(n):
                 n_dec, n_ret, n_done, n_hit, m = (int(v) for v in c[i])

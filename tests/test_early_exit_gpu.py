@@ -263,3 +263,48 @@ def test_continuous_bookkeeping_matches_host_reference(torch, with_net):
         net.close()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n_runs,with_logits", [(5000, True), (4096, False), (3, True), (1, False)])
+def test_exit_scan_matches_its_definition(torch, n_runs, with_logits):
+    """chym_exit_scan_device against the decision rule written out in numpy: runs reseeded
+    at assorted steps (so their local steps differ), energies on and off the reference,
+    logits on both sides of the threshold; counts and the restart order exactly."""
+    N, D, K, k_dec = 8, 2, 40, 4
+    J = inputs.sk_pm1(N, 3)
+    ctx = chym.Context(J, D)
+    prm = chym.Params(eps=0.1, prec=chym.PREC_BF16X2)
+    n_h = 1
+    ctx.run(prm, inputs.pump_grid(0.5, n_h), inputs.run_seeds(5, n_runs), 0, chym.Schedule(0, 0, K))
+    rng = np.random.default_rng(n_runs)
+    k_now = 0
+    for k_next in (4, 16, 40, 44):       # reseed random subsets at a few steps
+        ctx.run(prm, None, None, k_next - k_now, chym.Schedule(0, 0, K), n_runs=n_runs)
+        k_now = k_next
+        m = int(rng.integers(0, n_runs + 1))
+        if m:
+            runs = torch.from_numpy(np.sort(rng.choice(n_runs, m, replace=False)).astype(np.int32)).cuda()
+            sd = torch.from_numpy(inputs.run_seeds(77 + k_now, m).view(np.int64)).cuda()
+            ctx.reseed_device(runs.data_ptr(), m, sd.data_ptr(), prm.init_std)
+    offs = torch.empty(n_runs, dtype=torch.int64, device="cuda")
+    ctx.offsets_device(offs.data_ptr())
+    local = k_now - offs.cpu().numpy()
+    E_gs = -20.0
+    E = np.where(rng.random(n_runs) < 0.3, E_gs, E_gs + 4.0 * rng.integers(1, 5, n_runs))
+    L = rng.standard_normal(n_runs).astype(np.float32)
+    theta = 0.1
+    dE, dL = torch.from_numpy(E).cuda(), torch.from_numpy(L).cuda()
+    counts = torch.zeros(5, dtype=torch.int64, device="cuda")
+    order = torch.empty(n_runs, dtype=torch.int32, device="cuda")
+    ctx.exit_scan_device(dE.data_ptr(), E_gs, dL.data_ptr() if with_logits else 0, theta, K, k_dec,
+                         counts.data_ptr(), order.data_ptr())
+    done = local >= K
+    at_dec = (local == k_dec) & with_logits
+    retire = at_dec & (L < theta)
+    hit = done & (np.abs(E - E_gs) <= 1e-9 * abs(E_gs))
+    restart = done | retire
+    want = [int(at_dec.sum()), int(retire.sum()), int(done.sum()), int(hit.sum()), int(restart.sum())]
+    assert counts.cpu().tolist() == want
+    ref = np.concatenate([np.flatnonzero(restart), np.flatnonzero(~restart)])
+    assert np.array_equal(order.cpu().numpy(), ref)
+    ctx.close()
