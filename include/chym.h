@@ -326,7 +326,8 @@ CHYM_API chym_status chym_batch_status(chym_batch* b);
  * one step.  chym_batch_tune measures these costs on the current device for the
  * batch's own contexts at the split they run with: the whole batch is integrated
  * for probe_steps steps (once to warm up, then a few rounds timed per part with CUDA
- * events); after each round every part's cost is re-estimated from its measured
+ * events, each part's time the shorter of two runs); after each round every part's
+ * cost is re-estimated from its measured
  * time and CTA count, which moves the next split towards equal finish times, and
  * the split whose slowest part was fastest is kept.  Every context's state, step
  * and energies are restored afterwards, so tuning does not change any result.

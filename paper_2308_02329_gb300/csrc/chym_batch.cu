@@ -37,7 +37,7 @@ struct chym_batch {
   // one step on the small-N path, per dimension D; and one (128-row tile x K chunk
   // of 64) advanced one step on the large-N path.  The defaults were measured on a
   // GB300; chym_batch_tune re-measures them for the batch's own contexts.
-  double chunk_cost[9] = {0, 1.10, 0.64, 0.91, 1.01, 1.27, 1.43, 1.60, 1.76};
+  double chunk_cost[9] = {0, 1.10, 0.555, 0.89, 1.07, 1.27, 1.43, 1.60, 1.76};
   double k2_cost = 1.05;
   bool tuned = false;
   // Tile shapes (0: the kernels' defaults), chosen by chym_batch_tune's search or set by
@@ -372,8 +372,9 @@ CHYM_API chym_status chym_batch_run(chym_batch* b, const chym_params* params,
 
 // Autotuner: measure the planner's cost model on this device, for the batch's own
 // contexts and at the split it will run with.  The whole batch runs for probe_steps
-// steps (once untimed to warm up, then a few times timed per part with CUDA events);
-// after each timed run every part's cost is re-estimated from its measured time at
+// steps (once untimed to warm up, then a few rounds timed per part with CUDA events,
+// each part's time the shorter of two runs, so that one slow run does not decide);
+// after each round every part's cost is re-estimated from its measured time at
 // its CTA count (SM-microseconds per unit of work), which moves the next split
 // towards equal finish times.  The split with the shortest slowest part is kept.
 // The states, steps and energies of the contexts are saved before and restored after.
@@ -420,31 +421,36 @@ CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
   if (e != cudaSuccess) status = cuda_fail(e, "chym_batch_tune: events");
   double best_chunk[9], best_k2 = b->k2_cost, best_T = INFINITY;
   for (int D = 0; D <= 8; ++D) best_chunk[D] = b->chunk_cost[D];
-  constexpr int kRounds = 4;
+  constexpr int kRounds = 4, kReps = 2;
   for (int round = -1; round < kRounds && status == CHYM_OK; ++round) {
-    b->timing = round >= 0;
-    status = chym_batch_run(b, params, schedules, probe_steps, st);
-    if (status != CHYM_OK) break;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-      status = cuda_fail(e, "chym_batch_tune: probe");
-      break;
+    double T[9];
+    bool seen[9] = {};
+    for (int p = 0; p <= 8; ++p) T[p] = INFINITY;
+    for (int rep = 0; rep < (round < 0 ? 1 : kReps) && status == CHYM_OK; ++rep) {
+      b->timing = round >= 0;
+      status = chym_batch_run(b, params, schedules, probe_steps, st);
+      if (status != CHYM_OK) break;
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "chym_batch_tune: probe");
+        break;
+      }
+      status = chym_batch_status(b);
+      if (status != CHYM_OK || round < 0) break;
+      for (int p = 0; p <= 8; ++p) {
+        if (!b->timed[p]) continue;
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, b->t_begin[p], b->t_end[p]);
+        if (e != cudaSuccess) break;
+        T[p] = std::min(T[p], 1e3 * (double)ms);
+        seen[p] = true;
+      }
+      if (e != cudaSuccess) status = cuda_fail(e, "chym_batch_tune: timing");
     }
-    status = chym_batch_status(b);
     if (status != CHYM_OK || round < 0) continue;
-    double T_max = 0.0, T[9] = {0};
-    for (int p = 0; p <= 8; ++p) {
-      if (!b->timed[p]) continue;
-      float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, b->t_begin[p], b->t_end[p]);
-      if (e != cudaSuccess) break;
-      T[p] = 1e3 * (double)ms;
-      T_max = std::max(T_max, T[p]);
-    }
-    if (e != cudaSuccess) {
-      status = cuda_fail(e, "chym_batch_tune: timing");
-      break;
-    }
+    double T_max = 0.0;
+    for (int p = 0; p <= 8; ++p)
+      if (seen[p]) T_max = std::max(T_max, T[p]);
     if (T_max < best_T) {  // the split of this round is the best so far
       best_T = T_max;
       for (int D = 0; D <= 8; ++D) best_chunk[D] = b->chunk_cost[D];
@@ -452,7 +458,7 @@ CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
     }
     // re-estimate each part's cost at its operating point
     for (int p = 0; p <= 8; ++p) {
-      if (!b->timed[p] || b->part_units[p] <= 0.0 || T[p] <= 0.0) continue;
+      if (!seen[p] || b->part_units[p] <= 0.0) continue;
       const double c = T[p] * (double)b->part_ctas[p] / (b->part_units[p] * (double)probe_steps);
       if (p == 0) b->k2_cost = c;
       else b->chunk_cost[p] = c;
@@ -467,17 +473,20 @@ CHYM_API chym_status chym_batch_tune(chym_batch* b, const chym_params* params,
     for (int D = 0; D <= 8; ++D) b->chunk_cost[D] = best_chunk[D];
     b->k2_cost = best_k2;
     auto probe = [&](int part, double* t_out) -> chym_status {
-      chym_status r = chym_batch_run(b, params, schedules, probe_steps, st);
-      if (r != CHYM_OK) return r;
-      cudaError_t ce = cudaStreamSynchronize(st);
-      if (ce != cudaSuccess) return cuda_fail(ce, "chym_batch_tune: shape probe");
-      r = chym_batch_status(b);
-      if (r != CHYM_OK) return r;
-      float ms = 0.f;
-      if (!b->timed[part]) return fail(CHYM_ESTATE, "chym_batch_tune: part not timed");
-      ce = cudaEventElapsedTime(&ms, b->t_begin[part], b->t_end[part]);
-      if (ce != cudaSuccess) return cuda_fail(ce, "chym_batch_tune: timing");
-      *t_out = (double)ms;
+      *t_out = INFINITY;
+      for (int rep = 0; rep < kReps; ++rep) {  // the shorter of two runs
+        chym_status r = chym_batch_run(b, params, schedules, probe_steps, st);
+        if (r != CHYM_OK) return r;
+        cudaError_t ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "chym_batch_tune: shape probe");
+        r = chym_batch_status(b);
+        if (r != CHYM_OK) return r;
+        float ms = 0.f;
+        if (!b->timed[part]) return fail(CHYM_ESTATE, "chym_batch_tune: part not timed");
+        ce = cudaEventElapsedTime(&ms, b->t_begin[part], b->t_end[part]);
+        if (ce != cudaSuccess) return cuda_fail(ce, "chym_batch_tune: timing");
+        *t_out = std::min(*t_out, (double)ms);
+      }
       return CHYM_OK;
     };
     bool large[9] = {}, small[9] = {};

@@ -451,22 +451,18 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
           a_pending = false;
           tc_fence_after();
           if (ok) {
-            for (int ks = 0; ks < ksteps; ++ks) {
-              const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
-              mma_bf16(tmem + acc_col, da, smem_desc(bhi_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
-                       idesc, ks > 0);
-            }
-            for (int ks = 0; ks < ksteps; ++ks) {
-              const uint64_t da = smem_desc(a_base + (uint32_t)ks * 256u, 128u, a_sbo);
-              mma_bf16(tmem + acc_col, da, smem_desc(blo_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
-                       idesc, 1u);
-            }
+            // a K step moves only the 14-bit start-address field of each descriptor
+            // (shared addresses stay below 256 KB, so the field never carries)
+            const uint64_t da0 = smem_desc(a_base, 128u, a_sbo), dj0 = smem_desc(a_base + a_bytes, 128u, a_sbo);
+            const uint64_t dh0 = smem_desc(bhi_base, lbo_b, 128u), dl0 = smem_desc(blo_base, lbo_b, 128u);
+            const uint64_t sa = 256u >> 4, sb = (2u * lbo_b) >> 4;
+            for (int ks = 0; ks < ksteps; ++ks)
+              mma_bf16(tmem + acc_col, da0 + ks * sa, dh0 + ks * sb, idesc, ks > 0);
+            for (int ks = 0; ks < ksteps; ++ks)
+              mma_bf16(tmem + acc_col, da0 + ks * sa, dl0 + ks * sb, idesc, 1u);
             if (d.a_terms > 1) {
-              for (int ks = 0; ks < ksteps; ++ks) {
-                const uint64_t da = smem_desc(a_base + a_bytes + (uint32_t)ks * 256u, 128u, a_sbo);
-                mma_bf16(tmem + acc_col, da, smem_desc(bhi_base + (uint32_t)ks * 2u * lbo_b, lbo_b, 128u),
-                         idesc, 1u);
-              }
+              for (int ks = 0; ks < ksteps; ++ks)
+                mma_bf16(tmem + acc_col, dj0 + ks * sa, dh0 + ks * sb, idesc, 1u);
             }
             // (test of the timeout path: the completion signal goes elsewhere, so the
             // group's wait below runs out; the drain after the loop waits for it)
