@@ -285,8 +285,8 @@ def step_roofline(jobs, prec, steps_total, dur, clock_info, peaks, peak_src, pre
 # kernels as they stand (dram__bytes_read.sum + dram__bytes_write.sum), by workload and
 # precision: None where no capture of the current kernel exists.
 TRAFFIC = {
-    ("n100", "bf16x2"): (3.22e7, "the three step_tc_kernel launches of one bench step (D = 2, 3, 4; "
-                                 "6.9 + 11.1 + 14.2 MB read, writes stay in L2)"),
+    ("n100", "bf16x2"): (3.25e7, "the three step_tc_kernel launches of one bench step (D = 2, 3, 4; "
+                                 "7.5 + 10.8 + 14.2 MB read, writes stay in L2)"),
     ("sk800", "fp8"): (2.972e9, "one step_k2_kernel launch (one integration step): 1486 MB captured "
                                 "on 32768 runs, doubled for 65536 (traffic grows with the columns)"),
 }
