@@ -327,6 +327,10 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
   __shared__ uint4 s_rk[G][RG][5];  // Philox round keys of each run
   __shared__ int64_t s_koff[G][RG];  // each run's (re)seeding step
   __shared__ int s_kuni[G];           // 1 when all runs of the group share one offset
+  // when they do not: each run's local step and annealing scale at the current step,
+  // double buffered by step parity (written one step ahead by the run's own thread)
+  __shared__ __align__(16) int64_t s_kl[2][G][RG];
+  __shared__ __align__(8) float s_rp[2][G][RG];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = warp >> 2, wq = warp & 3;
@@ -413,6 +417,19 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
       *reinterpret_cast<uint4*>(Bhi + o) = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();  // every zero must land before any thread writes its state into B
     if (p < nr && s_koff[g][p] != s_koff[g][0]) s_kuni[g] = 0;
+    // run p's local step at step kk (noise counter) and its annealing scale alpha_mu
+    // (mu >= 1), for the per-run path
+    auto put_step = [&](int64_t kk) {
+      if (p < RG) {
+        const int64_t kl = kk - s_koff[g][p];
+        float rp = 1.f;
+        if (d.sched_kind == 1 && kl >= d.k_anneal)
+          rp = kl >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(kl - d.k_anneal) * d.inv_ramp);
+        s_kl[kk & 1][g][p] = kl;
+        s_rp[kk & 1][g][p] = rp;
+      }
+    };
+    put_step(d.k0);  // read after the barrier below
     const bool live = p < N;
     const float edt_p = d.edt * ((d.w && live) ? (float)d.w[p] : 1.f);  // dt eps times the spin's weight
     // ---- load the state: X[run][p][mu] -> TMEM master + BF16 hi/lo B ----
@@ -509,15 +526,12 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
                 int64_t klA = kl_u, klB = kl_u;
                 float rA = ramp_u, rB = ramp_u;
                 if (!k_uniform) {
-                  klA = k - s_koff[g][r];
-                  klB = k - s_koff[g][r + 1];
-                  rA = rB = 1.f;
-                }
-                if (!k_uniform && d.sched_kind == 1) {
-                  if (klA >= d.k_anneal)
-                    rA = klA >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(klA - d.k_anneal) * d.inv_ramp);
-                  if (klB >= d.k_anneal)
-                    rB = klB >= d.k_total ? 0.f : fmaxf(0.f, 1.f - (float)(klB - d.k_anneal) * d.inv_ramp);
+                  const longlong2 kl2 = *reinterpret_cast<const longlong2*>(&s_kl[k & 1][g][r]);
+                  const float2 rp2 = *reinterpret_cast<const float2*>(&s_rp[k & 1][g][r]);
+                  klA = kl2.x;
+                  klB = kl2.y;
+                  rA = rp2.x;
+                  rB = rp2.y;
                 }
                 const float2 e0 = make_float2(edt_p, edt_p), e1 = make_float2(edt_p * rA, edt_p * rB);
                 float2 z[4 * ((D + 3) / 4)];
@@ -542,7 +556,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
                   // and the quad transposes the normals
                   if ((j & 3) == 0) {
                     const int m = p & 3, rm = r + m;
-                    const int64_t klm = k_uniform ? kl_u : k - s_koff[g][rm];
+                    const int64_t klm = k_uniform ? kl_u : s_kl[k & 1][g][rm];
                     const uint4 w = philox_rk(noise_counter((uint32_t)p >> 2, 0u, 0u, (uint64_t)klm), s_rk[g][rm]);
                     float2 zc, zs;  // normals (0, 2) and (1, 3) of the block
                     box_muller_x2(w.x, w.y, w.z, w.w, neg2ln2s2, zc, zs);
@@ -588,6 +602,7 @@ __global__ void __launch_bounds__(512, 1) step_tc_kernel(TcLaunch L) {
             }
           }
         }
+        if (!k_uniform) put_step(k + 1);  // the other parity: nobody reads it in this step
         tmem_wait_st();
         fence_async_smem();
         tc_fence_before();
