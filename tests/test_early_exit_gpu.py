@@ -265,7 +265,7 @@ def test_continuous_bookkeeping_matches_host_reference(torch, with_net):
     b.close()
 
 
-@pytest.mark.parametrize("n_runs,with_logits", [(5000, True), (4096, False), (3, True), (1, False)])
+@pytest.mark.parametrize("n_runs,with_logits", [(65536, True), (5000, True), (4096, False), (3, True), (1, False)])
 def test_exit_scan_matches_its_definition(torch, n_runs, with_logits):
     """chym_exit_scan_device against the decision rule written out in numpy: runs reseeded
     at assorted steps (so their local steps differ), energies on and off the reference,
